@@ -1,0 +1,98 @@
+"""Pins of the oracle's dense BEM (assembly + LU) against closed forms and identities.
+
+* Pressurised spherical cavity: the discrete radial displacement approaches the closed form as
+  the icosphere is refined (discretisation-limited, not a 1e-6 pin: centroids of the flat
+  triangles lie inside the sphere and the fixed 7-point near rule has a mesh-independent error).
+* Reproduction of an exact exterior field: the Stokes field of a point load placed inside the
+  cavity solves the elastodynamic equations in the medium and decays, so it satisfies the BIE;
+  prescribing its traction (Neumann), displacement (Dirichlet) or a mix must return the other
+  half at the collocation points.  A wrong column sign or a swapped block fails this.
+* Static rigid-body identity for the exterior problem, 1/2 I + sum_e H_ie = I (s -> 0).
+* LU residual and the near-list definition.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import bem, closed_form as CF, kernels as K
+
+MAT = W.CAVITY_MATERIAL
+
+
+def _radial_error(level, s):
+    P = W.spherical_cavity(level=level)
+    g = bem.geometry(P.verts, P.tris)
+    x, _, _ = bem.solve(g, s, MAT, P.bc_type, P.bc_value)
+    ur = -np.einsum("ij,ij->i", x.reshape(-1, 3), g.normal)
+    ex = CF.cavity_ur(s, 1.0, MAT.mu, MAT.nu, MAT.rho, W.CAVITY_P0)
+    return abs(ur.mean() - ex) / abs(ex)
+
+
+@pytest.mark.parametrize("s", [250.0 + 0j, 250.0 + 1570.8j])
+def test_cavity_converges_to_closed_form(s):
+    e1, e2 = _radial_error(1, s), _radial_error(2, s)
+    assert e2 < 0.6 * e1
+    assert e2 < 0.05
+
+
+def _point_load_field(g, s, src, direction):
+    d = g.centroid - src
+    u = np.einsum("i,nij->nj", direction, K.fundamental_U(d, s, MAT.mu, MAT.nu, MAT.rho))
+    t = np.einsum("i,nij->nj", direction,
+                  K.fundamental_T(d, g.normal, s, MAT.mu, MAT.nu, MAT.rho))
+    return u, t
+
+
+@pytest.mark.parametrize("split", ["neumann", "dirichlet", "mixed"])
+def test_exact_exterior_field_is_reproduced(split):
+    v, f = W.icosphere(2, 1.0)
+    g = bem.geometry(v, f)
+    s = 250.0 + 3000.0j
+    src = np.array([0.1, -0.2, 0.15])
+    direction = np.array([0.3, 0.5, -0.8])
+    direction /= np.linalg.norm(direction)
+    u, t = _point_load_field(g, s, src, direction)
+    if split == "neumann":
+        bc = np.zeros(len(f), dtype=np.int8)
+    elif split == "dirichlet":
+        bc = np.ones(len(f), dtype=np.int8)
+    else:
+        bc = (g.centroid[:, 2] > 0).astype(np.int8)
+    known = np.where(bc[:, None] == bem.NEUMANN, t, u)
+    unknown = np.where(bc[:, None] == bem.NEUMANN, u, t)
+    # the known data are complex, so assemble A and apply the known-data blocks directly
+    A, _ = bem.assemble(g, s, MAT, bc, np.zeros_like(known.real), profile=bem.PROFILE_CONSTANT)
+    ne = len(f)
+    Hb, Gb = bem.element_blocks(g, s, MAT)
+    Hb = Hb + 0.5 * np.eye(3)[None, None] * np.eye(ne)[:, :, None, None]
+    neu = bc == bem.NEUMANN
+    Kb = np.where(neu[None, :, None, None], Gb, -Hb).transpose(0, 2, 1, 3).reshape(3 * ne, 3 * ne)
+    x = np.linalg.solve(A, Kb @ known.reshape(-1)).reshape(ne, 3)
+    rel = np.linalg.norm(x - unknown) / np.linalg.norm(unknown)
+    assert rel < 0.05, rel
+
+
+def test_static_rigid_body_identity():
+    v, f = W.icosphere(2, 1.0)
+    g = bem.geometry(v, f)
+    H, _ = bem.element_blocks(g, 1e-4, MAT, rows=[0, 7, 123])
+    rs = H.sum(axis=1) + 0.5 * np.eye(3)
+    assert np.abs(rs - np.eye(3)).max() < 5e-3
+
+
+def test_lu_residual():
+    P = W.spherical_cavity(level=1)
+    g = bem.geometry(P.verts, P.tris)
+    x, A, b = bem.solve(g, P.s[5], MAT, P.bc_type, P.bc_value)
+    assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) < 1e-13
+
+
+def test_near_lists_definition():
+    v, f = W.icosphere(2, 1.0)
+    g = bem.geometry(v, f)
+    rp, cols = bem.near_lists(g)
+    ne = len(f)
+    for i in range(0, ne, 37):
+        ref = [e for e in range(ne) if e != i and
+               np.linalg.norm(g.centroid[i] - g.centroid[e]) < 2.0 * g.h[e]]
+        assert list(cols[rp[i]:rp[i + 1]]) == ref

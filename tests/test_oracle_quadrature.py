@@ -1,0 +1,138 @@
+"""Pins of the oracle's quadrature rules and singular element integrals.
+
+Rules: exactness on barycentric monomials (int_T l1^a l2^b l3^c dA = 2|T| a! b! c!/(a+b+c+2)!).
+Self integrals: against brute-force polar-coordinate integration around the collocation point
+(a different mapping from the Duffy squares and the edge formula the oracle uses), and the
+CPV against its polar form int_0^{2pi} rh(theta) ln R(theta) dtheta.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import bem, kernels as K, quadrature as Q
+
+MAT = W.CAVITY_MATERIAL
+
+
+def _tri(seed=0):
+    rng = np.random.default_rng(seed)
+    p = rng.standard_normal((3, 3))
+    return p
+
+
+def _bary_integral(a, b, c, area):
+    return 2 * area * math.factorial(a) * math.factorial(b) * math.factorial(c) / math.factorial(
+        a + b + c + 2)
+
+
+@pytest.mark.parametrize("rule,degree", [(Q.rule_4pt, 3), (Q.rule_7pt, 5)])
+def test_triangle_rules_exact_on_monomials(rule, degree):
+    bary, w = rule()
+    assert abs(w.sum() - 1.0) < 1e-15
+    p = _tri()
+    area = 0.5 * np.linalg.norm(np.cross(p[1] - p[0], p[2] - p[0]))
+    for a in range(degree + 1):
+        for b in range(degree + 1 - a):
+            for c in range(degree + 1 - a - b):
+                approx = area * np.sum(w * bary[:, 0] ** a * bary[:, 1] ** b * bary[:, 2] ** c)
+                assert abs(approx - _bary_integral(a, b, c, area)) < 1e-14 * area
+    # and it is NOT exact one degree higher (guards against a rule of the wrong order)
+    a = degree + 1
+    approx = area * np.sum(w * bary[:, 0] ** a)
+    assert abs(approx - _bary_integral(a, 0, 0, area)) > 1e-6 * area
+
+
+def _polar_setup(tri, x0, normal, n_theta=96, n_rho=96):
+    """Polar Gauss-Legendre points around x0 covering the flat triangle: theta split at the
+    vertex directions.  Returns unit directions u (m, 3), R(theta) (m,), theta weights (m,) and
+    the 1-D rule on [0, 1] for rho / R."""
+    t1 = (tri[0] - x0) / np.linalg.norm(tri[0] - x0)
+    t2 = np.cross(normal, t1)
+    ang = []
+    for v in tri:
+        d = v - x0
+        ang.append(math.atan2(d @ t2, d @ t1) % (2 * math.pi))
+    ang = sorted(ang) + [sorted(ang)[0] + 2 * math.pi]
+    g, gw = Q.gauss_legendre_01(n_theta)
+    th, tw = [], []
+    for a0, a1 in zip(ang[:-1], ang[1:]):
+        th.append(a0 + (a1 - a0) * g)
+        tw.append((a1 - a0) * gw)
+    th, tw = np.concatenate(th), np.concatenate(tw)
+    u = np.cos(th)[:, None] * t1 + np.sin(th)[:, None] * t2
+    # distance to the boundary along u: smallest positive hit on the three edge lines
+    R = np.full(len(th), np.inf)
+    for k in range(3):
+        a, b = tri[k], tri[(k + 1) % 3]
+        e = b - a
+        # solve x0 + rho u = a + tau e (in-plane)
+        for m in range(len(th)):
+            M = np.stack([u[m], -e, normal], axis=1)
+            rho, tau, _ = np.linalg.solve(M, a - x0)
+            if rho > 1e-14 and -1e-12 <= tau <= 1 + 1e-12:
+                R[m] = min(R[m], rho)
+    gr, grw = Q.gauss_legendre_01(n_rho)
+    return u, R, tw, gr, grw
+
+
+@pytest.mark.parametrize("s", [250.0 + 0.0j, 250.0 + 8000.0j])
+def test_self_integrals_vs_polar_brute_force(s):
+    v, f = W.icosphere(1, 1.0)
+    g = bem.geometry(v, f)
+    for i in (0, 17):
+        tri, x0, nrm = g.p[i], g.centroid[i], g.normal[i]
+        # make the element less regular so the CPV is not zero by symmetry
+        tri = tri.copy()
+        tri[1] = tri[1] + 0.3 * (tri[1] - tri[0])
+        x0 = tri.mean(axis=0)
+        gi = bem.Geometry(p=tri[None], centroid=x0[None], normal=nrm[None],
+                          area=np.array([1.0]), h=np.array([1.0]), q4=None, w4=None, q7=None,
+                          w7=None)
+        H, G = bem.self_blocks(gi, 0, s, MAT)                 # the configured 13 x 13 rule
+        H48, G48 = bem.self_blocks(gi, 0, s, MAT, n=48)       # same code, converged rule
+        u, R, tw, gr, grw = _polar_setup(tri, x0, nrm)
+        rho = R[:, None] * gr[None, :]                          # (m, k)
+        d = rho[..., None] * u[:, None, :]
+        wt = (tw[:, None] * R[:, None] * grw[None, :])          # d theta d rho
+        Ub = K.fundamental_U(d, s, MAT.mu, MAT.nu, MAT.rho)
+        G_ref = np.einsum("mk,mkij->ij", wt * rho, Ub)
+        Tb = K.fundamental_T(d, nrm, s, MAT.mu, MAT.nu, MAT.rho)
+        f0 = K.kelvin_T(u, nrm, MAT.nu)                        # rho^2 T0, independent of rho
+        inner = np.einsum("mk,mkij->mij", wt, rho[..., None, None] * Tb - f0[:, None] / rho[..., None, None])
+        H_ref = inner.sum(axis=0) + np.einsum("m,mij->ij", tw * np.log(R), f0)
+        # the implementation is exact up to the rule: converged Duffy == polar brute force
+        assert np.abs(G48 - G_ref).max() / np.abs(G_ref).max() < 1e-11
+        assert np.abs(H48 - H_ref).max() / np.abs(H_ref).max() < 1e-11
+        # and the configured 13 x 13 rule is within its own quadrature error (this element is
+        # ~0.6 m across, so at 8000 rad/s the integrand oscillates over it)
+        assert np.abs(G - G_ref).max() / np.abs(G_ref).max() < 5e-5
+        assert np.abs(H - H_ref).max() / np.abs(H_ref).max() < 5e-5
+
+
+def test_cpv_zero_on_equilateral_and_polar_form():
+    h = math.sqrt(3) / 2
+    tri = np.array([[0, 0, 0], [1, 0, 0], [0.5, h, 0]], dtype=float)
+    n = np.array([0, 0, 1.0])
+    assert np.abs(bem.cpv_rh_over_r2(tri.mean(0), tri, n)).max() < 1e-14
+    tri2 = np.array([[0, 0, 0], [1.3, 0.1, 0], [0.2, 0.7, 0]], dtype=float)
+    x0 = tri2.mean(0) + np.array([0.05, -0.02, 0])
+    C = bem.cpv_rh_over_r2(x0, tri2, n)
+    u, R, tw, _, _ = _polar_setup(tri2, x0, n)
+    C_ref = np.einsum("m,mk->k", tw * np.log(R), u)
+    assert np.abs(C - C_ref).max() < 1e-12
+
+
+def test_duffy_integrates_inverse_distance():
+    """int_T dA / r over the triangle (x0, a, b) = p (asinh(t2/p) - asinh(t1/p))."""
+    rng = np.random.default_rng(3)
+    x0, a, b = rng.standard_normal((3, 3))
+    pts, w = Q.duffy_points(x0, a, b, 13)
+    approx = np.sum(w / np.linalg.norm(pts - x0, axis=1))
+    t = (b - a) / np.linalg.norm(b - a)
+    t1 = (a - x0) @ t
+    t2 = t1 + np.linalg.norm(b - a)
+    p = np.linalg.norm((a - x0) - t1 * t)
+    exact = p * (math.asinh(t2 / p) - math.asinh(t1 / p))
+    assert abs(approx - exact) < 1e-12 * exact
