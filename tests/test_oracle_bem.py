@@ -43,9 +43,8 @@ def _point_load_field(g, s, src, direction):
     return u, t
 
 
-@pytest.mark.parametrize("split", ["neumann", "dirichlet", "mixed"])
-def test_exact_exterior_field_is_reproduced(split):
-    v, f = W.icosphere(2, 1.0)
+def _reproduction_error(level, split):
+    v, f = W.icosphere(level, 1.0)
     g = bem.geometry(v, f)
     s = 250.0 + 3000.0j
     src = np.array([0.1, -0.2, 0.15])
@@ -68,8 +67,16 @@ def test_exact_exterior_field_is_reproduced(split):
     neu = bc == bem.NEUMANN
     Kb = np.where(neu[None, :, None, None], Gb, -Hb).transpose(0, 2, 1, 3).reshape(3 * ne, 3 * ne)
     x = np.linalg.solve(A, Kb @ known.reshape(-1)).reshape(ne, 3)
-    rel = np.linalg.norm(x - unknown) / np.linalg.norm(unknown)
-    assert rel < 0.05, rel
+    return np.linalg.norm(x - unknown) / np.linalg.norm(unknown)
+
+
+@pytest.mark.parametrize("split", ["neumann", "dirichlet", "mixed"])
+def test_exact_exterior_field_is_reproduced(split):
+    """Discretisation error of the reproduced field falls with refinement (measured: ~0.22 on
+    80 triangles, ~0.075 on 320, ~0.03 on 1280) -- a sign or block error would stay O(1)."""
+    e1, e2 = _reproduction_error(1, split), _reproduction_error(2, split)
+    assert e2 < 0.5 * e1
+    assert e2 < 0.1, e2
 
 
 def test_static_rigid_body_identity():
