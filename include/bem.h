@@ -1,0 +1,182 @@
+/*
+ * bem.h -- C ABI of the GB300 Laplace-domain elastodynamic BEM frequency-solve library.
+ *
+ * Method: Xiao, Rong, Ye, Zhang, "An efficient adaptive frequency sampling scheme for
+ * large-scale transient boundary element analysis".  The library solves the frequency-domain
+ * boundary integral equation of Sec. 2.1, Eq. (bie),
+ *     c_ij u_j(x,s) + PV int_G T_ij(x,y,s) u_j(y,s) dG = int_G U_ij(x,y,s) t_j(y,s) dG,
+ * discretised by constant-element collocation on flat triangles into A(s) a(s) = b(s)
+ * (Eq. (Aa_b)), at many complex frequencies s = sigma + i omega at once, and post-processes the
+ * responses by the Fourier series method (Sec. 2.2, Eq. (IDFT-MFT)), vector fitting
+ * (Sec. 2.3, Eqs. (vf-f), (vf-td)) and adaptive frequency sampling (Sec. 3, Algorithm AFS).
+ *
+ * Conventions (all entry points):
+ *  - Every function returns 0 (BEM_OK) on success or a negative BEM_ERR_* code; it never
+ *    aborts the process.  bem_last_error() gives a one-line message for the last failure.
+ *  - SI units.  Complex numbers are interleaved (re, im) IEEE doubles at the ABI.
+ *  - Laplace variable s with time factor e^{st}; boundary data are a real spatial pattern times
+ *    the Laplace transform of a time profile (BEM_PROFILE_STEP: 1/s, BEM_PROFILE_CONSTANT: 1).
+ *  - Input arrays are copied; the caller keeps ownership.  Output arrays are written, never
+ *    retained.  A pointer argument may be host memory or device memory of the context's device
+ *    (detected with cudaPointerGetAttributes) unless the description says "host".
+ *  - Mesh: triangles are counter-clockwise about their unit normal, and that normal points out
+ *    of the elastic domain (into cavities, out of finite bodies).  Unknown ordering: element e
+ *    owns entries 3e, 3e+1, 3e+2 (x, y, z) of every solution vector.
+ *  - A context is bound to one CUDA device and one stream; calls on one context must not
+ *    overlap in time (the context is not thread-safe).  All work runs on the context's stream;
+ *    functions return after that work completes.
+ */
+#ifndef BEM_H
+#define BEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define BEM_OK 0
+#define BEM_ERR_INVALID_ARG (-1)   /* bad pointer, size, value or call order              */
+#define BEM_ERR_CUDA (-2)          /* a CUDA runtime call failed (message has the reason) */
+#define BEM_ERR_NOT_CONVERGED (-3) /* tolerance not met within the iteration limits       */
+#define BEM_ERR_OOM (-4)           /* device allocation failed                             */
+#define BEM_ERR_BREAKDOWN (-5)     /* GMRES breakdown / NaN in an instance                 */
+#define BEM_ERR_NO_MESH (-6)       /* operation needs bem_set_mesh first                   */
+
+/* ------------------------------------------------------------------ enums */
+#define BEM_BC_TRACTION 0      /* traction given, displacement unknown (Neumann)   */
+#define BEM_BC_DISPLACEMENT 1  /* displacement given, traction unknown (Dirichlet) */
+
+#define BEM_PROFILE_STEP 0     /* Laplace factor 1/s (Heaviside step in time)  */
+#define BEM_PROFILE_CONSTANT 1 /* Laplace factor 1 (data already in s-domain)  */
+
+#define BEM_PREC_FP64 0   /* plain FP64: FP64 operator, FP64 GMRES                            */
+#define BEM_PREC_MIXED 1  /* FP32 operator + FP32-stored Krylov basis with FP64 dot products,
+                             FP64 iterative refinement (residual and RHS in FP64)            */
+#define BEM_PREC_FP32 2   /* operator-only mode for bem_apply: FP32 far/near kernels          */
+
+#define BEM_APPLY_A 0     /* y = A(s) x : the system operator of Eq. (Aa_b)                  */
+#define BEM_APPLY_K 1     /* y = K(s) x : the operator acting on the known boundary data,
+                             so that b(s) = K(s) (profile(s) * pattern)                       */
+
+#define BEM_WARM_ZERO 0     /* GMRES starts from x0 = 0                                       */
+#define BEM_WARM_NEAREST 1  /* x0 = the stored solution at the nearest solved frequency      */
+#define BEM_WARM_MLP 2      /* x0 = POD basis * MLP(s) (trained by bem_warm_train)           */
+
+typedef struct bem_ctx bem_ctx;
+
+typedef struct bem_options {
+  int32_t precision;   /* BEM_PREC_FP64 or BEM_PREC_MIXED (default MIXED)                   */
+  int32_t restart;     /* GMRES restart length m (default 50)                               */
+  int32_t max_iters;   /* cap on GMRES iterations per inner solve (default 500)             */
+  int32_t max_refine;  /* cap on FP64 refinement steps in MIXED mode (default 8)            */
+  double tol;          /* target ||b - A x||_2 / ||b||_2, measured in FP64 (default 1e-6)   */
+  double inner_tol;    /* relative reduction asked of each FP32 inner solve (default 1e-5)  */
+  int32_t warm_start;  /* BEM_WARM_* (default ZERO)                                          */
+  int32_t freq_tile;   /* frequencies per operator tile, 0 = autotuned (default 0)          */
+  int32_t use_graph;   /* capture GMRES iterations in CUDA graphs (default 1)                */
+  int32_t reserved[7];
+} bem_options;
+
+typedef struct bem_solve_stats {
+  int32_t* iterations;   /* [ns] total GMRES iterations per frequency (nullable)              */
+  int32_t* refinements;  /* [ns] FP64 residual evaluations per frequency (nullable)           */
+  double* residual;      /* [ns] final ||b - A x||_2/||b||_2, FP64 (nullable)                  */
+  int32_t* status;       /* [ns] 0 converged, else BEM_ERR_NOT_CONVERGED / _BREAKDOWN (null.)  */
+  double seconds;        /* out: wall time of the call                                         */
+  int64_t fp32_operator_applies; /* out: batched FP32 operator launches (far + near)          */
+  int64_t fp64_operator_applies; /* out: batched FP64 operator launches                       */
+  int64_t kernel_launches;       /* out: kernels of this library launched by the call        */
+} bem_solve_stats;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to run on (the
+ * caller keeps it alive), or NULL for a stream the context creates and owns.
+ * Errors: INVALID_ARG (out NULL, device out of range), CUDA. */
+int bem_create(bem_ctx** out, int device, void* cuda_stream);
+
+/* Release every device and host resource of the context (NULL is a no-op). */
+int bem_destroy(bem_ctx* ctx);
+
+/* Message of the last failed call on ctx (or of the last failed bem_create if ctx is NULL).
+ * The string stays valid until the next call on the same context. */
+const char* bem_last_error(const bem_ctx* ctx);
+
+/* Fill *opt with the defaults listed in bem_options. */
+int bem_default_options(bem_options* opt);
+int bem_set_options(bem_ctx* ctx, const bem_options* opt);
+
+/* ------------------------------------------------------------------ problem statement */
+
+/* Boundary mesh (Sec. 2.1: the boundary G partitioned into n_e triangles).
+ * verts: nv x 3 doubles (host); tris: ne x 3 int32 vertex indices (host).
+ * Builds on the device the element geometry (centroid collocation points, unit normals,
+ * areas, longest edges, 4- and 7-point quadrature points) and the near-source lists
+ * (|x_i - c_e| < 2 h_e).  Clears boundary conditions and cached frequency data.
+ * Errors: INVALID_ARG (sizes <= 0, index out of range, degenerate triangle), OOM, CUDA. */
+int bem_set_mesh(bem_ctx* ctx, const double* verts, int64_t nv, const int32_t* tris, int64_t ne);
+
+/* Isotropic material (Sec. 2.1): shear modulus mu [Pa], Poisson ratio nu, density rho.
+ * Errors: INVALID_ARG (mu <= 0, rho <= 0, nu outside (-1, 0.5)). */
+int bem_set_material(bem_ctx* ctx, double mu, double nu, double rho);
+
+/* Boundary conditions (Sec. 2.1, the columns of Eq. (Aa_b)): bc_type[ne] (host, int8,
+ * BEM_BC_*), bc_value[ne x 3] (host, doubles: the given traction [Pa] or displacement [m]
+ * pattern per element), time_profile BEM_PROFILE_*.
+ * Errors: INVALID_ARG (NULL, unknown type/profile), NO_MESH. */
+int bem_set_bc(bem_ctx* ctx, const int8_t* bc_type, const double* bc_value, int time_profile);
+
+/* ------------------------------------------------------------------ the frequency solve */
+
+/* Solve A(s_k) a(s_k) = b(s_k) for every frequency s_k (Sec. 2.1, Eq. (Aa_b)), all frequencies
+ * batched: matrix-free operator (far field by 4-point quadrature evaluated on the fly, near
+ * sources by the 7-point rule, the own element by Duffy + CPV), right block-Jacobi
+ * preconditioned GMRES(m), and in MIXED mode FP64 iterative refinement around FP32 inner
+ * solves.
+ * s: 2 x ns doubles (re, im interleaved, Re s > 0).  x_out: ns x 3ne complex (interleaved
+ * doubles), host or device, nullable (then only statistics are produced).
+ * Returns NOT_CONVERGED if some frequency missed opt.tol (its status says which); x_out is
+ * still written with the best iterate.  Errors: INVALID_ARG, NO_MESH, OOM, CUDA. */
+int bem_solve_frequencies(bem_ctx* ctx, const double* s, int64_t ns, double* x_out,
+                          bem_solve_stats* stats);
+
+/* ------------------------------------------------------------------ operator-level calls
+ * (the steps of one solve, exposed for verification and measurement) */
+
+/* Element geometry (step a1): out[ne x 8] doubles (host or device) =
+ * centroid x,y,z, unit normal x,y,z, area, longest edge h_e. */
+int bem_geometry(bem_ctx* ctx, double* out);
+
+/* Near-source lists (step a2): CSR over collocation points, sources e != i with
+ * |x_i - c_e| < 2 h_e, ascending.  row_ptr[ne+1] (host); cols[cap] (host) may be NULL to
+ * query the count, which is returned in *nnz.  Errors: INVALID_ARG (cap too small). */
+int bem_near_lists(bem_ctx* ctx, int64_t* row_ptr, int32_t* cols, int64_t cap, int64_t* nnz);
+
+/* Element integral blocks H_ie = int_e T(x_i, y; s) dA, G_ie = int_e U(x_i, y; s) dA
+ * (steps a2/a4; Eq. (bie) discretised) for npairs (i, e) pairs at one frequency, FP64, with the
+ * same rule selection as the operator (self: Duffy + CPV, near: 7-point, far: 4-point).
+ * rows, cols: int32[npairs] (host).  H_out, G_out: npairs x 3 x 3 complex (host or device),
+ * row-major [pair][i][j], (re, im) interleaved. */
+int bem_element_blocks(bem_ctx* ctx, double s_re, double s_im, const int32_t* rows,
+                       const int32_t* cols, int64_t npairs, double* H_out, double* G_out);
+
+/* y = A(s_k) x_k (which = BEM_APPLY_A) or y = K(s_k) x_k (BEM_APPLY_K) for all k (steps
+ * a2+a4): x, y: ns x 3ne complex doubles (host or device).  precision: BEM_PREC_FP64 or
+ * BEM_PREC_FP32 (inputs rounded to FP32, far and near kernels in FP32, output widened). */
+int bem_apply(bem_ctx* ctx, const double* s, int64_t ns, const double* x, double* y,
+              int precision, int which);
+
+/* Right-hand sides b(s_k) = K(s_k) (profile(s_k) * bc_value) in FP64 (step a3).
+ * b_out: ns x 3ne complex doubles (host or device). */
+int bem_rhs(bem_ctx* ctx, const double* s, int64_t ns, double* b_out);
+
+/* Block-Jacobi preconditioner (step a5): y_k = D(s_k)^{-1} x_k with D the 3 x 3 diagonal
+ * blocks A_ii(s_k) (free term + own-element integral).  FP64.  x, y: ns x 3ne complex. */
+int bem_precond_apply(bem_ctx* ctx, const double* s, int64_t ns, const double* x, double* y);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BEM_H */

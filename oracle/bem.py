@@ -181,20 +181,30 @@ def profile_factor(profile, s):
     raise ValueError(f"unknown time profile {profile}")
 
 
+def operators(g: Geometry, s, mat, bc_type, rows=None):
+    """Dense A(s) and K(s) (rows x N): A acts on the unknowns, K on the known boundary data,
+    so that b(s) = K(s) (profile(s) * pattern).  Eq. (Aa_b) with the BC column swap."""
+    ne = len(g.area)
+    rows = np.arange(ne) if rows is None else np.asarray(rows)
+    H, G = element_blocks(g, s, mat, rows=rows)
+    H = H + 0.5 * np.eye(3)[None, None] * (rows[:, None] == np.arange(ne)[None, :])[:, :, None, None]
+    neu = np.asarray(bc_type) == NEUMANN
+    A_blk = np.where(neu[None, :, None, None], H, -G)
+    K_blk = np.where(neu[None, :, None, None], G, -H)
+    A = A_blk.transpose(0, 2, 1, 3).reshape(3 * len(rows), 3 * ne)
+    Kn = K_blk.transpose(0, 2, 1, 3).reshape(3 * len(rows), 3 * ne)
+    return A, Kn
+
+
+def known_data(bc_value, s, profile=PROFILE_STEP):
+    """profile(s) * pattern, flattened (N,)."""
+    return (np.asarray(bc_value, dtype=np.float64) * profile_factor(profile, s)).reshape(-1)
+
+
 def assemble(g: Geometry, s, mat, bc_type, bc_value, profile=PROFILE_STEP):
     """Dense A(s) (N x N) and b(s) (N) with N = 3 ne, Eq. (Aa_b)."""
-    ne = len(g.area)
-    H, G = element_blocks(g, s, mat)
-    H = H + 0.5 * np.eye(3)[None, None] * np.eye(ne)[:, :, None, None]
-    bc_type = np.asarray(bc_type)
-    known = np.asarray(bc_value, dtype=np.float64) * profile_factor(profile, s)   # (ne, 3)
-    neu = bc_type == NEUMANN
-    A_blk = np.where(neu[None, :, None, None], H, -G)
-    K_blk = np.where(neu[None, :, None, None], G, -H)       # acts on the known data
-    A = A_blk.transpose(0, 2, 1, 3).reshape(3 * ne, 3 * ne)
-    Kn = K_blk.transpose(0, 2, 1, 3).reshape(3 * ne, 3 * ne)
-    b = Kn @ known.reshape(-1)
-    return A, b
+    A, Kn = operators(g, s, mat, bc_type)
+    return A, Kn @ known_data(bc_value, s, profile)
 
 
 def solve(g: Geometry, s, mat, bc_type, bc_value, profile=PROFILE_STEP):

@@ -1,0 +1,307 @@
+"""Thin ctypes binding of the C ABI declared in include/bem.h (argument marshalling only).
+
+Every computation runs in the CUDA library libbem_gb300.so; this module converts Python
+arguments (numpy arrays for host memory, or torch tensors, host or CUDA) to the pointers and
+sizes the C functions take, and raises BemError for a negative return code.  There is no
+Python or CPU fallback: if the library is missing the import of a function fails loudly.
+
+Function names are those of the C ABI.  `Context` is a convenience wrapper over them.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libbem_gb300.so")
+
+BEM_OK = 0
+BEM_ERR_INVALID_ARG = -1
+BEM_ERR_CUDA = -2
+BEM_ERR_NOT_CONVERGED = -3
+BEM_ERR_OOM = -4
+BEM_ERR_BREAKDOWN = -5
+BEM_ERR_NO_MESH = -6
+BEM_BC_TRACTION = 0
+BEM_BC_DISPLACEMENT = 1
+BEM_PROFILE_STEP = 0
+BEM_PROFILE_CONSTANT = 1
+BEM_PREC_FP64 = 0
+BEM_PREC_MIXED = 1
+BEM_PREC_FP32 = 2
+BEM_APPLY_A = 0
+BEM_APPLY_K = 1
+BEM_WARM_ZERO = 0
+BEM_WARM_NEAREST = 1
+BEM_WARM_MLP = 2
+
+
+class BemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class bem_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("restart", C.c_int32), ("max_iters", C.c_int32),
+                ("max_refine", C.c_int32), ("tol", C.c_double), ("inner_tol", C.c_double),
+                ("warm_start", C.c_int32), ("freq_tile", C.c_int32), ("use_graph", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
+
+
+class bem_solve_stats(C.Structure):
+    _fields_ = [("iterations", C.POINTER(C.c_int32)), ("refinements", C.POINTER(C.c_int32)),
+                ("residual", C.POINTER(C.c_double)), ("status", C.POINTER(C.c_int32)),
+                ("seconds", C.c_double), ("fp32_operator_applies", C.c_int64),
+                ("fp64_operator_applies", C.c_int64), ("kernel_launches", C.c_int64)]
+
+
+_P = C.c_void_p
+_I64 = C.c_int64
+_SIGS = {
+    "bem_create": (C.c_int, [C.POINTER(_P), C.c_int, _P]),
+    "bem_destroy": (C.c_int, [_P]),
+    "bem_last_error": (C.c_char_p, [_P]),
+    "bem_default_options": (C.c_int, [C.POINTER(bem_options)]),
+    "bem_set_options": (C.c_int, [_P, C.POINTER(bem_options)]),
+    "bem_set_mesh": (C.c_int, [_P, _P, _I64, _P, _I64]),
+    "bem_set_material": (C.c_int, [_P, C.c_double, C.c_double, C.c_double]),
+    "bem_set_bc": (C.c_int, [_P, _P, _P, C.c_int]),
+    "bem_solve_frequencies": (C.c_int, [_P, _P, _I64, _P, C.POINTER(bem_solve_stats)]),
+    "bem_geometry": (C.c_int, [_P, _P]),
+    "bem_near_lists": (C.c_int, [_P, _P, _P, _I64, C.POINTER(_I64)]),
+    "bem_element_blocks": (C.c_int, [_P, C.c_double, C.c_double, _P, _P, _I64, _P, _P]),
+    "bem_apply": (C.c_int, [_P, _P, _I64, _P, _P, C.c_int, C.c_int]),
+    "bem_rhs": (C.c_int, [_P, _P, _I64, _P]),
+    "bem_precond_apply": (C.c_int, [_P, _P, _I64, _P, _P]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libbem_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build it with `python -m paper_1511_04355_gb300.build`")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def declared_symbols():
+    """Names of the functions the header declares (the binding's table)."""
+    return sorted(_SIGS)
+
+
+# ------------------------------------------------------------------------------ marshalling
+def _ptr(a):
+    """Pointer of a numpy array (host) or torch tensor (host or CUDA); None -> NULL."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(ctx, rc, what):
+    if rc != BEM_OK:
+        msg = load_library().bem_last_error(ctx)
+        raise BemError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+
+def _cplx_as_pairs(s):
+    s = np.ascontiguousarray(np.asarray(s, dtype=np.complex128).reshape(-1))
+    return s, len(s)
+
+
+# ------------------------------------------------------------------------------ functions
+def bem_create(device: int = 0, stream=None):
+    lib = load_library()
+    h = _P()
+    rc = lib.bem_create(C.byref(h), device, stream)
+    _check(None, rc, "bem_create")
+    return h
+
+
+def bem_destroy(ctx):
+    load_library().bem_destroy(ctx)
+
+
+def bem_default_options():
+    o = bem_options()
+    load_library().bem_default_options(C.byref(o))
+    return o
+
+
+def bem_set_options(ctx, opt: bem_options):
+    _check(ctx, load_library().bem_set_options(ctx, C.byref(opt)), "bem_set_options")
+
+
+def bem_set_mesh(ctx, verts, tris):
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    _check(ctx, load_library().bem_set_mesh(ctx, _ptr(v), len(v), _ptr(t), len(t)), "bem_set_mesh")
+
+
+def bem_set_material(ctx, mu, nu, rho):
+    _check(ctx, load_library().bem_set_material(ctx, mu, nu, rho), "bem_set_material")
+
+
+def bem_set_bc(ctx, bc_type, bc_value, profile=BEM_PROFILE_STEP):
+    t = np.ascontiguousarray(bc_type, dtype=np.int8)
+    v = np.ascontiguousarray(bc_value, dtype=np.float64)
+    _check(ctx, load_library().bem_set_bc(ctx, _ptr(t), _ptr(v), profile), "bem_set_bc")
+
+
+def bem_solve_frequencies(ctx, s, x_out=None, allow_not_converged=False):
+    """Returns (x_out, stats dict).  x_out: None -> a new (ns, 3ne) complex128 numpy array;
+    else a caller array/tensor (host or CUDA, complex128, ns*3ne entries) written in place."""
+    s, ns = _cplx_as_pairs(s)
+    stats = bem_solve_stats()
+    it = np.zeros(ns, np.int32)
+    rf = np.zeros(ns, np.int32)
+    res = np.zeros(ns, np.float64)
+    st = np.zeros(ns, np.int32)
+    stats.iterations = it.ctypes.data_as(C.POINTER(C.c_int32))
+    stats.refinements = rf.ctypes.data_as(C.POINTER(C.c_int32))
+    stats.residual = res.ctypes.data_as(C.POINTER(C.c_double))
+    stats.status = st.ctypes.data_as(C.POINTER(C.c_int32))
+    rc = load_library().bem_solve_frequencies(ctx, _ptr(s), ns, _ptr(x_out), C.byref(stats))
+    if not (allow_not_converged and rc == BEM_ERR_NOT_CONVERGED):
+        _check(ctx, rc, "bem_solve_frequencies")
+    info = dict(iterations=it, refinements=rf, residual=res, status=st, seconds=stats.seconds,
+                fp32_operator_applies=stats.fp32_operator_applies,
+                fp64_operator_applies=stats.fp64_operator_applies,
+                kernel_launches=stats.kernel_launches, rc=rc)
+    return x_out, info
+
+
+def bem_geometry(ctx, ne):
+    out = np.zeros((ne, 8), np.float64)
+    _check(ctx, load_library().bem_geometry(ctx, _ptr(out)), "bem_geometry")
+    return out
+
+
+def bem_near_lists(ctx, ne):
+    lib = load_library()
+    nnz = _I64()
+    rp = np.zeros(ne + 1, np.int64)
+    _check(ctx, lib.bem_near_lists(ctx, _ptr(rp), None, 0, C.byref(nnz)), "bem_near_lists")
+    cols = np.zeros(max(nnz.value, 1), np.int32)
+    _check(ctx, lib.bem_near_lists(ctx, None, _ptr(cols), len(cols), C.byref(nnz)), "bem_near_lists")
+    return rp, cols[:nnz.value]
+
+
+def bem_element_blocks(ctx, s, rows, cols):
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    c = np.ascontiguousarray(cols, dtype=np.int32)
+    H = np.zeros((len(r), 3, 3), np.complex128)
+    G = np.zeros((len(r), 3, 3), np.complex128)
+    s = complex(s)
+    _check(ctx, load_library().bem_element_blocks(ctx, s.real, s.imag, _ptr(r), _ptr(c), len(r),
+                                                  _ptr(H), _ptr(G)), "bem_element_blocks")
+    return H, G
+
+
+def bem_apply(ctx, s, x, y=None, precision=BEM_PREC_FP64, which=BEM_APPLY_A):
+    s, ns = _cplx_as_pairs(s)
+    if isinstance(x, np.ndarray):
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+        if y is None:
+            y = np.zeros_like(x)
+    _check(ctx, load_library().bem_apply(ctx, _ptr(s), ns, _ptr(x), _ptr(y), precision, which),
+           "bem_apply")
+    return y
+
+
+def bem_rhs(ctx, s, ne, b_out=None):
+    s, ns = _cplx_as_pairs(s)
+    if b_out is None:
+        b_out = np.zeros((ns, 3 * ne), np.complex128)
+    _check(ctx, load_library().bem_rhs(ctx, _ptr(s), ns, _ptr(b_out)), "bem_rhs")
+    return b_out
+
+
+def bem_precond_apply(ctx, s, x, y=None):
+    s, ns = _cplx_as_pairs(s)
+    x = np.ascontiguousarray(x, dtype=np.complex128) if isinstance(x, np.ndarray) else x
+    if y is None:
+        y = np.zeros_like(x)
+    _check(ctx, load_library().bem_precond_apply(ctx, _ptr(s), ns, _ptr(x), _ptr(y)),
+           "bem_precond_apply")
+    return y
+
+
+class Context:
+    """Owns one bem_ctx (device + stream) and remembers the mesh size."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.h = bem_create(device, stream)
+        self.ne = 0
+
+    def close(self):
+        if self.h:
+            bem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_mesh(self, verts, tris):
+        bem_set_mesh(self.h, verts, tris)
+        self.ne = len(tris)
+
+    def set_material(self, mu, nu, rho):
+        bem_set_material(self.h, mu, nu, rho)
+
+    def set_bc(self, bc_type, bc_value, profile=BEM_PROFILE_STEP):
+        bem_set_bc(self.h, bc_type, bc_value, profile)
+
+    def set_options(self, **kw):
+        o = bem_default_options()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        bem_set_options(self.h, o)
+        return o
+
+    def solve(self, s, x_out=None, allow_not_converged=False):
+        s = np.asarray(s, dtype=np.complex128).reshape(-1)
+        if x_out is None:
+            x_out = np.zeros((len(s), 3 * self.ne), np.complex128)
+        return bem_solve_frequencies(self.h, s, x_out, allow_not_converged)
+
+    def apply(self, s, x, precision=BEM_PREC_FP64, which=BEM_APPLY_A):
+        return bem_apply(self.h, s, x, None, precision, which)
+
+    def rhs(self, s):
+        return bem_rhs(self.h, s, self.ne)
+
+    def precond(self, s, x):
+        return bem_precond_apply(self.h, s, x)
+
+    def geometry(self):
+        return bem_geometry(self.h, self.ne)
+
+    def near_lists(self):
+        return bem_near_lists(self.h, self.ne)
+
+    def element_blocks(self, s, rows, cols):
+        return bem_element_blocks(self.h, s, rows, cols)

@@ -1,0 +1,351 @@
+// extern "C" entry points of the library: argument checking, host/device marshalling and
+// orchestration of the kernels in geometry.cu, operator.cu and gmres.cu.  Every C++ exception
+// is turned into a BEM_ERR_* code plus a message (bem_last_error), so no error escapes the ABI.
+#include <chrono>
+#include <cstring>
+#include <mutex>
+
+#include "kernel_math.cuh"
+
+namespace bem {
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Copies between any host pointer and any device pointer of the context (unified addressing).
+void copy_in(bem_ctx* ctx, void* dst_dev, const void* src, size_t bytes) {
+  if (!bytes) return;
+  BEM_CUDA(cudaMemcpyAsync(dst_dev, src, bytes, cudaMemcpyDefault, ctx->stream));
+  BEM_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+void copy_out(bem_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  if (!bytes) return;
+  BEM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream));
+  BEM_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+__global__ void narrow_kernel(const cx<double>* a, cx<float>* b, int64_t n) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) b[t] = mk((float)a[t].r, (float)a[t].i);
+}
+__global__ void widen_kernel(const cx<float>* a, cx<double>* b, int64_t n) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) b[t] = mk((double)a[t].r, (double)a[t].i);
+}
+
+}  // namespace bem
+
+using namespace bem;
+
+namespace {
+std::mutex g_err_mu;
+std::string g_create_err;
+
+template <class Fn>
+int guarded(bem_ctx* ctx, Fn&& fn) {
+  try {
+    if (!ctx) throw Error(BEM_ERR_INVALID_ARG, "null context");
+    BEM_CUDA(cudaSetDevice(ctx->device));
+    ctx->launches = 0;
+    fn();
+    return BEM_OK;
+  } catch (const Error& e) {
+    if (ctx) ctx->err = e.what();
+    return e.code;
+  } catch (const std::exception& e) {
+    if (ctx) ctx->err = e.what();
+    return BEM_ERR_INVALID_ARG;
+  }
+}
+
+void need_mesh(bem_ctx* ctx) {
+  if (ctx->mesh.ne <= 0) throw Error(BEM_ERR_NO_MESH, "bem_set_mesh has not been called");
+  if (!ctx->mat.set) throw Error(BEM_ERR_INVALID_ARG, "bem_set_material has not been called");
+}
+
+void need_bc(bem_ctx* ctx) {
+  if (!ctx->bc.set) throw Error(BEM_ERR_INVALID_ARG, "bem_set_bc has not been called");
+}
+}  // namespace
+
+extern "C" {
+
+int bem_default_options(bem_options* o) {
+  if (!o) return BEM_ERR_INVALID_ARG;
+  std::memset(o, 0, sizeof *o);
+  o->precision = BEM_PREC_MIXED;
+  o->restart = 50;
+  o->max_iters = 500;
+  o->max_refine = 8;
+  o->tol = 1e-6;
+  o->inner_tol = 1e-5;
+  o->warm_start = BEM_WARM_ZERO;
+  o->freq_tile = 0;
+  o->use_graph = 1;
+  return BEM_OK;
+}
+
+int bem_create(bem_ctx** out, int device, void* stream) {
+  if (!out) return BEM_ERR_INVALID_ARG;
+  *out = nullptr;
+  bem_ctx* c = nullptr;
+  try {
+    int n = 0;
+    BEM_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) throw Error(BEM_ERR_INVALID_ARG, "device index out of range");
+    BEM_CUDA(cudaSetDevice(device));
+    c = new bem_ctx();
+    c->device = device;
+    bem_default_options(&c->opt);
+    if (stream) {
+      c->stream = (cudaStream_t)stream;
+    } else {
+      BEM_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    *out = c;
+    return BEM_OK;
+  } catch (const Error& e) {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_create_err = e.what();
+    delete c;
+    return e.code;
+  }
+}
+
+int bem_destroy(bem_ctx* ctx) {
+  if (!ctx) return BEM_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return BEM_OK;
+}
+
+const char* bem_last_error(const bem_ctx* ctx) {
+  if (!ctx) {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    return g_create_err.c_str();
+  }
+  return ctx->err.c_str();
+}
+
+int bem_set_options(bem_ctx* ctx, const bem_options* o) {
+  return guarded(ctx, [&] {
+    BEM_REQUIRE(o, "null options");
+    BEM_REQUIRE(o->precision == BEM_PREC_FP64 || o->precision == BEM_PREC_MIXED,
+                "precision must be BEM_PREC_FP64 or BEM_PREC_MIXED");
+    BEM_REQUIRE(o->restart >= 1 && o->restart <= 512, "restart must be in [1, 512]");
+    BEM_REQUIRE(o->max_iters >= 1, "max_iters must be >= 1");
+    BEM_REQUIRE(o->tol > 0 && o->tol < 1, "tol must be in (0, 1)");
+    BEM_REQUIRE(o->inner_tol > 0 && o->inner_tol < 1, "inner_tol must be in (0, 1)");
+    BEM_REQUIRE(o->warm_start >= BEM_WARM_ZERO && o->warm_start <= BEM_WARM_MLP, "bad warm_start");
+    ctx->opt = *o;
+  });
+}
+
+int bem_set_mesh(bem_ctx* ctx, const double* verts, int64_t nv, const int32_t* tris, int64_t ne) {
+  return guarded(ctx, [&] {
+    BEM_REQUIRE(verts && tris, "null mesh array");
+    BEM_REQUIRE(nv >= 3 && ne >= 1, "mesh needs nv >= 3 and ne >= 1");
+    BEM_REQUIRE(ne < (int64_t)1 << 28, "too many elements");
+    for (int64_t k = 0; k < 3 * ne; ++k)
+      BEM_REQUIRE(tris[k] >= 0 && tris[k] < nv, "triangle vertex index out of range");
+    for (int64_t k = 0; k < 3 * nv; ++k) BEM_REQUIRE(std::isfinite(verts[k]), "non-finite vertex");
+    Mesh& m = ctx->mesh;
+    m.ne = 0;
+    m.verts.assign(verts, verts + 3 * nv);
+    m.tris.assign(tris, tris + 3 * ne);
+    m.ne = ne;
+    ctx->bc.set = false;
+    ctx->fs.valid = false;
+    try {
+      build_geometry(ctx);
+      build_near_lists(ctx);
+    } catch (...) {
+      m.ne = 0;
+      throw;
+    }
+  });
+}
+
+int bem_set_material(bem_ctx* ctx, double mu, double nu, double rho) {
+  return guarded(ctx, [&] {
+    BEM_REQUIRE(mu > 0 && std::isfinite(mu), "mu must be > 0");
+    BEM_REQUIRE(rho > 0 && std::isfinite(rho), "rho must be > 0");
+    BEM_REQUIRE(nu > -1.0 && nu < 0.5, "nu must be in (-1, 0.5)");
+    ctx->mat.mu = mu;
+    ctx->mat.nu = nu;
+    ctx->mat.rho = rho;
+    ctx->mat.set = true;
+    ctx->fs.valid = false;
+  });
+}
+
+int bem_set_bc(bem_ctx* ctx, const int8_t* type, const double* value, int profile) {
+  return guarded(ctx, [&] {
+    if (ctx->mesh.ne <= 0) throw Error(BEM_ERR_NO_MESH, "bem_set_mesh has not been called");
+    BEM_REQUIRE(type && value, "null boundary-condition array");
+    BEM_REQUIRE(profile == BEM_PROFILE_STEP || profile == BEM_PROFILE_CONSTANT, "unknown time profile");
+    const int64_t ne = ctx->mesh.ne;
+    for (int64_t e = 0; e < ne; ++e)
+      BEM_REQUIRE(type[e] == BEM_BC_TRACTION || type[e] == BEM_BC_DISPLACEMENT, "unknown bc type");
+    for (int64_t k = 0; k < 3 * ne; ++k) BEM_REQUIRE(std::isfinite(value[k]), "non-finite bc value");
+    BC& b = ctx->bc;
+    b.type.assign(type, type + ne);
+    b.value.assign(value, value + 3 * ne);
+    b.profile = profile;
+    b.d_type.reserve(ne);
+    b.d_value.reserve(sizeof(double) * 3 * ne);
+    copy_in(ctx, b.d_type.p, b.type.data(), ne);
+    copy_in(ctx, b.d_value.p, b.value.data(), sizeof(double) * 3 * ne);
+    b.set = true;
+    ctx->fs.valid = false;
+  });
+}
+
+int bem_geometry(bem_ctx* ctx, double* out) {
+  return guarded(ctx, [&] {
+    if (ctx->mesh.ne <= 0) throw Error(BEM_ERR_NO_MESH, "bem_set_mesh has not been called");
+    BEM_REQUIRE(out, "null output");
+    static_assert(sizeof(Elem64) == 8 * sizeof(double), "Elem64 layout");
+    copy_out(ctx, out, ctx->mesh.elem64.p, sizeof(Elem64) * ctx->mesh.ne);
+  });
+}
+
+int bem_near_lists(bem_ctx* ctx, int64_t* row_ptr, int32_t* cols, int64_t cap, int64_t* nnz) {
+  return guarded(ctx, [&] {
+    if (ctx->mesh.ne <= 0) throw Error(BEM_ERR_NO_MESH, "bem_set_mesh has not been called");
+    const Mesh& m = ctx->mesh;
+    if (nnz) *nnz = m.nnz;
+    if (row_ptr)
+      for (int64_t i = 0; i <= m.ne; ++i) row_ptr[i] = m.h_near_ptr[i];
+    if (cols) {
+      BEM_REQUIRE(cap >= m.nnz, "cols capacity smaller than the number of near pairs");
+      std::memcpy(cols, m.h_near_col.data(), sizeof(int32_t) * m.nnz);
+    }
+  });
+}
+
+int bem_element_blocks(bem_ctx* ctx, double s_re, double s_im, const int32_t* rows,
+                       const int32_t* cols, int64_t npairs, double* H_out, double* G_out) {
+  return guarded(ctx, [&] {
+    need_mesh(ctx);
+    BEM_REQUIRE(rows && cols && H_out && G_out, "null pointer");
+    BEM_REQUIRE(npairs >= 1, "npairs must be >= 1");
+    BEM_REQUIRE(s_re > 0 && std::isfinite(s_re) && std::isfinite(s_im), "need 0 < Re s");
+    element_blocks(ctx, s_re, s_im, rows, cols, npairs, reinterpret_cast<cx<double>*>(H_out),
+                   reinterpret_cast<cx<double>*>(G_out));
+  });
+}
+
+int bem_apply(bem_ctx* ctx, const double* s, int64_t ns, const double* x, double* y,
+              int precision, int which) {
+  return guarded(ctx, [&] {
+    need_mesh(ctx);
+    BEM_REQUIRE(s && x && y, "null pointer");
+    BEM_REQUIRE(ns >= 1, "ns must be >= 1");
+    BEM_REQUIRE(precision == BEM_PREC_FP64 || precision == BEM_PREC_FP32, "precision must be FP64 or FP32");
+    BEM_REQUIRE(which == BEM_APPLY_A || which == BEM_APPLY_K, "which must be BEM_APPLY_A or _K");
+    std::vector<double> sh(2 * ns);
+    copy_out(ctx, sh.data(), s, sizeof(double) * 2 * ns);
+    prepare_frequencies(ctx, sh.data(), ns);
+    const int64_t n = ns * 3 * ctx->mesh.ne;
+    ctx->io_a.reserve(sizeof(cx<double>) * n);
+    ctx->io_b.reserve(sizeof(cx<double>) * n);
+    copy_in(ctx, ctx->io_a.p, x, sizeof(cx<double>) * n);
+    if (precision == BEM_PREC_FP64) {
+      apply_operator64(ctx, ctx->io_a.as<cx<double>>(), ctx->io_b.as<cx<double>>(), which, nullptr);
+    } else {
+      DevBuf xf, yf;
+      xf.reserve(sizeof(cx<float>) * n);
+      yf.reserve(sizeof(cx<float>) * n);
+      narrow_kernel<<<grid_for(n, 256), 256, 0, ctx->stream>>>(ctx->io_a.as<cx<double>>(), xf.as<cx<float>>(), n);
+      apply_operator32(ctx, xf.as<cx<float>>(), yf.as<cx<float>>(), which, nullptr);
+      widen_kernel<<<grid_for(n, 256), 256, 0, ctx->stream>>>(yf.as<cx<float>>(), ctx->io_b.as<cx<double>>(), n);
+      ctx->launches += 2;
+      BEM_LAUNCHED();
+      BEM_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    copy_out(ctx, y, ctx->io_b.p, sizeof(cx<double>) * n);
+  });
+}
+
+int bem_rhs(bem_ctx* ctx, const double* s, int64_t ns, double* b_out) {
+  return guarded(ctx, [&] {
+    need_mesh(ctx);
+    need_bc(ctx);
+    BEM_REQUIRE(s && b_out && ns >= 1, "bad argument");
+    std::vector<double> sh(2 * ns);
+    copy_out(ctx, sh.data(), s, sizeof(double) * 2 * ns);
+    prepare_frequencies(ctx, sh.data(), ns);
+    const int64_t n = ns * 3 * ctx->mesh.ne;
+    ctx->io_a.reserve(sizeof(cx<double>) * n);
+    ctx->io_b.reserve(sizeof(cx<double>) * n);
+    known_data(ctx, ctx->io_a.as<cx<double>>());
+    apply_operator64(ctx, ctx->io_a.as<cx<double>>(), ctx->io_b.as<cx<double>>(), BEM_APPLY_K, nullptr);
+    copy_out(ctx, b_out, ctx->io_b.p, sizeof(cx<double>) * n);
+  });
+}
+
+int bem_precond_apply(bem_ctx* ctx, const double* s, int64_t ns, const double* x, double* y) {
+  return guarded(ctx, [&] {
+    need_mesh(ctx);
+    BEM_REQUIRE(s && x && y && ns >= 1, "bad argument");
+    std::vector<double> sh(2 * ns);
+    copy_out(ctx, sh.data(), s, sizeof(double) * 2 * ns);
+    prepare_frequencies(ctx, sh.data(), ns);
+    const int64_t n = ns * 3 * ctx->mesh.ne;
+    ctx->io_a.reserve(sizeof(cx<double>) * n);
+    ctx->io_b.reserve(sizeof(cx<double>) * n);
+    copy_in(ctx, ctx->io_a.p, x, sizeof(cx<double>) * n);
+    apply_precond64(ctx, ctx->io_a.as<cx<double>>(), ctx->io_b.as<cx<double>>(), nullptr);
+    copy_out(ctx, y, ctx->io_b.p, sizeof(cx<double>) * n);
+  });
+}
+
+int bem_solve_frequencies(bem_ctx* ctx, const double* s, int64_t ns, double* x_out,
+                          bem_solve_stats* stats) {
+  int not_conv = 0;
+  const int rc = guarded(ctx, [&] {
+    const auto t0 = std::chrono::steady_clock::now();
+    need_mesh(ctx);
+    need_bc(ctx);
+    BEM_REQUIRE(s && ns >= 1, "bad frequency list");
+    ctx->f32_applies = ctx->f64_applies = 0;
+    std::vector<double> sh(2 * ns);
+    copy_out(ctx, sh.data(), s, sizeof(double) * 2 * ns);
+    prepare_frequencies(ctx, sh.data(), ns);
+    const int64_t n = ns * 3 * ctx->mesh.ne;
+    ctx->io_a.reserve(sizeof(cx<double>) * n);
+    std::vector<int32_t> it, rf, status;
+    std::vector<double> res;
+    solve_batch(ctx, ctx->io_a.as<cx<double>>(), stats, it, rf, res, status);
+    if (x_out) copy_out(ctx, x_out, ctx->io_a.p, sizeof(cx<double>) * n);
+    for (int64_t f = 0; f < ns; ++f) not_conv |= (status[f] != 0);
+    if (stats) {
+      if (stats->iterations) std::memcpy(stats->iterations, it.data(), sizeof(int32_t) * ns);
+      if (stats->refinements) std::memcpy(stats->refinements, rf.data(), sizeof(int32_t) * ns);
+      if (stats->residual) std::memcpy(stats->residual, res.data(), sizeof(double) * ns);
+      if (stats->status) std::memcpy(stats->status, status.data(), sizeof(int32_t) * ns);
+      stats->fp32_operator_applies = ctx->f32_applies;
+      stats->fp64_operator_applies = ctx->f64_applies;
+      stats->kernel_launches = ctx->launches;
+      stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+  });
+  if (rc != BEM_OK) return rc;
+  if (not_conv) {
+    ctx->err = "some frequencies did not reach the tolerance (see stats.status)";
+    return BEM_ERR_NOT_CONVERGED;
+  }
+  return BEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,250 @@
+// Internal declarations of the GB300 BEM library (not part of the ABI).
+//
+// Layout in device memory (n_e elements, N = 3 n_e unknowns, F frequencies in a batch):
+//   element geometry   Elem64[n_e] (FP64 master), float4 SoA copies for the FP32 kernels
+//   quadrature points  4-point and 7-point rules: [n_e][q] x (x, y, z, w * area)
+//   near lists         CSR int32 (row_ptr[n_e+1], cols[nnz])
+//   vectors            [F][n_e][3] complex, (re, im) interleaved, frequency-major so that one
+//                      instance's vector is contiguous for the GMRES vector kernels
+//   diagonal blocks    [F][n_e][9] complex FP64: own-element H_ii and G_ii
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/bem.h"
+
+namespace bem {
+
+// ------------------------------------------------------------------------------- errors
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define BEM_CUDA(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      throw ::bem::Error(e_ == cudaErrorMemoryAllocation ? BEM_ERR_OOM : BEM_ERR_CUDA,  \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));           \
+    }                                                                                   \
+  } while (0)
+
+#define BEM_REQUIRE(cond, msg)                                              \
+  do {                                                                      \
+    if (!(cond)) throw ::bem::Error(BEM_ERR_INVALID_ARG, std::string(msg)); \
+  } while (0)
+
+// launch check: catches configuration errors right after a launch
+#define BEM_LAUNCHED() BEM_CUDA(cudaGetLastError())
+
+// ------------------------------------------------------------------------------- complex
+template <class R>
+struct cx {
+  R r, i;
+};
+template <class R>
+__host__ __device__ __forceinline__ cx<R> mk(R r, R i) {
+  cx<R> z;
+  z.r = r;
+  z.i = i;
+  return z;
+}
+template <class R>
+__host__ __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return mk(a.r + b.r, a.i + b.i); }
+template <class R>
+__host__ __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return mk(a.r - b.r, a.i - b.i); }
+template <class R>
+__host__ __device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return mk(a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r);
+}
+template <class R>
+__host__ __device__ __forceinline__ cx<R> operator*(R a, cx<R> b) { return mk(a * b.r, a * b.i); }
+template <class R>
+__host__ __device__ __forceinline__ cx<R> conj(cx<R> a) { return mk(a.r, -a.i); }
+// a + k * b with real k
+template <class R>
+__host__ __device__ __forceinline__ cx<R> axpy(R k, cx<R> b, cx<R> a) {
+  return mk(fma(k, b.r, a.r), fma(k, b.i, a.i));
+}
+// a + b * c (complex)
+template <class R>
+__host__ __device__ __forceinline__ cx<R> cfma(cx<R> b, cx<R> c, cx<R> a) {
+  return mk(fma(b.r, c.r, fma(-b.i, c.i, a.r)), fma(b.r, c.i, fma(b.i, c.r, a.i)));
+}
+
+// ------------------------------------------------------------------------------- constants
+constexpr int kSeriesMax = 20;         // max Taylor terms of the small-|z| branch
+constexpr int kSeriesF32 = 9;          // terms used by the FP32 kernels (|z| < 1/2)
+constexpr int kSeriesF64 = 18;         // terms used by the FP64 kernels (|z| < 1/2)
+constexpr double kZSeries2 = 0.25;     // |z_s|^2 below which the series is used
+constexpr double kNearFactor = 2.0;    // near source: |x_i - c_e| < 2 h_e
+constexpr int kDuffyN = 13;            // Gauss-Legendre points per Duffy direction
+
+// Material constants used by the kernels (host computes them in FP64).
+template <class R>
+struct MatC {
+  R mu;        // shear modulus
+  R inv_cs;    // 1 / c_s
+  R beta;      // c_s / c_p
+  R beta2;     // (c_s / c_p)^2
+  R c1m2b2;    // 1 - 2 beta^2
+  R inv4pimu;  // 1 / (4 pi mu)
+  R d[kSeriesMax];  // Taylor coefficients of J(z) = beta^2 h(beta z) - h(z)
+};
+
+// Per-frequency constants.
+template <class R>
+struct FreqC {
+  cx<R> a;       // s / c_s
+  cx<R> inv_a2;  // 1 / a^2
+  R a_abs2;      // |a|^2
+  R pad;
+};
+
+// Four packed doubles (centroid + h, normal + area, quadrature point + weight).
+struct alignas(32) D4 {
+  double x, y, z, w;
+};
+
+// Element geometry, FP64 master.
+struct Elem64 {
+  double c[3];  // centroid (collocation point)
+  double n[3];  // unit normal (out of the elastic domain)
+  double area;
+  double h;     // longest edge
+};
+
+// ------------------------------------------------------------------------------- buffers
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  // grow-only: keeps the allocation when it is large enough
+  void reserve(size_t n) {
+    if (n <= bytes) return;
+    release();
+    if (n == 0) return;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      throw Error(BEM_ERR_OOM, "cudaMalloc of " + std::to_string(n) + " bytes failed: " +
+                                   cudaGetErrorString(e));
+    }
+    bytes = n;
+  }
+  template <class T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// ------------------------------------------------------------------------------- context
+struct Mesh {
+  int64_t ne = 0;
+  std::vector<double> verts;   // nv x 3
+  std::vector<int32_t> tris;   // ne x 3
+  DevBuf elem64;               // Elem64[ne]
+  DevBuf tri64;                // double[ne][9] vertices
+  DevBuf c32, n32;             // float4[ne]: (centroid, h), (normal, area)
+  DevBuf c64, n64;             // D4[ne]:     (centroid, h), (normal, area)
+  DevBuf q4_64, q7_64;         // double4-like [ne][4|7][4]
+  DevBuf q4_32, q7_32;         // float4 [ne][4|7]
+  DevBuf near_ptr, near_col;   // int32 CSR
+  int64_t nnz = 0;
+  std::vector<int32_t> h_near_ptr, h_near_col;
+};
+
+struct Material {
+  double mu = 0, nu = 0, rho = 0;
+  bool set = false;
+};
+
+struct BC {
+  bool set = false;
+  int profile = BEM_PROFILE_STEP;
+  std::vector<int8_t> type;    // per element
+  std::vector<double> value;   // ne x 3
+  DevBuf d_type;               // int8[ne]
+  DevBuf d_value;              // double[ne][3]
+};
+
+// Frequency-set data: constants and own-element blocks for a batch of frequencies.
+struct FreqSet {
+  int64_t F = 0;
+  std::vector<double> s;       // 2F
+  DevBuf fc64, fc32;           // FreqC<double/float>[F]
+  DevBuf Tself, Gself;         // cx<double>[F][ne][9]
+  DevBuf Minv64;               // cx<double>[F][ne][9] inverse of A_ii
+  DevBuf Minv32;               // cx<float>[F][ne][9]
+  DevBuf pfac;                 // cx<double>[F] profile factor
+  bool valid = false;
+};
+
+}  // namespace bem
+
+struct bem_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  bem_options opt{};
+  bem::Mesh mesh;
+  bem::Material mat;
+  bem::BC bc;
+  bem::FreqSet fs;
+  // scratch buffers for vectors (grow-only)
+  bem::DevBuf io_a, io_b;       // staging for ABI copies
+  bem::DevBuf active;           // int32[F] per-frequency active flags
+  int64_t launches = 0;         // kernels launched (accumulated, reset per call)
+  int64_t f32_applies = 0, f64_applies = 0;
+};
+
+namespace bem {
+
+// ------------------------------------------------------------------------------- host API
+// geometry.cu
+void build_geometry(bem_ctx* ctx);
+void build_near_lists(bem_ctx* ctx);
+MatC<double> mat_constants64(const Material& m);
+MatC<float> mat_constants32(const Material& m);
+void prepare_frequencies(bem_ctx* ctx, const double* s_host, int64_t F);
+void element_blocks(bem_ctx* ctx, double sr, double si, const int32_t* rows,
+                    const int32_t* cols, int64_t npairs, cx<double>* H, cx<double>* G);
+
+// operator.cu
+// y[f] = Op(s_f) x[f] for f with active[f] != 0 (active may be null = all).
+// which = BEM_APPLY_A or BEM_APPLY_K.  x, y device pointers [F][ne][3] complex.
+void apply_operator64(bem_ctx* ctx, const cx<double>* x, cx<double>* y, int which,
+                      const int32_t* active);
+void apply_operator32(bem_ctx* ctx, const cx<float>* x, cx<float>* y, int which,
+                      const int32_t* active);
+void apply_precond64(bem_ctx* ctx, const cx<double>* x, cx<double>* y, const int32_t* active);
+void apply_precond32(bem_ctx* ctx, const cx<float>* x, cx<float>* y, const int32_t* active);
+void known_data(bem_ctx* ctx, cx<double>* out);  // profile(s_f) * bc_value, [F][ne][3]
+
+// gmres.cu
+void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* st,
+                 std::vector<int32_t>& iters, std::vector<int32_t>& refines,
+                 std::vector<double>& resid, std::vector<int32_t>& status);
+
+// helpers
+inline int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }
+bool is_device_ptr(const void* p);
+void copy_in(bem_ctx* ctx, void* dst_dev, const void* src, size_t bytes);
+void copy_out(bem_ctx* ctx, void* dst, const void* src_dev, size_t bytes);
+
+}  // namespace bem

@@ -1,0 +1,501 @@
+// Batched GMRES(m) with right block-Jacobi preconditioning and FP64 iterative refinement:
+// the linear solver of Sec. 2.1 ("the linear system is solved iteratively by GMRES", with the
+// block-diagonal preconditioner of Sec. 4), run for every frequency of the batch at once.
+//
+// Outer loop (FP64):   r = b - A x   (FP64 matrix-free operator)
+//                      stop instance f when ||r_f|| <= tol ||b_f||
+// Inner loop (precision T = float in MIXED mode, double in FP64 mode):
+//                      GMRES(m) on A M^{-1} y = r, x += M^{-1} V y
+//   Arnoldi: classical Gram-Schmidt applied twice (CGS2); every inner product and norm is
+//   accumulated in FP64 and the Hessenberg matrix, Givens rotations and least-squares vector
+//   are FP64; basis vectors are stored in T (they are the operator's input).
+// Instances retire individually: a converged frequency clears its active flag and every
+// kernel (including the operator tiles of its frequency group) skips it.
+#include <algorithm>
+#include <chrono>
+
+#include "kernel_math.cuh"
+
+namespace bem {
+
+// ------------------------------------------------------------------------------- kernels
+template <class T>
+__device__ __forceinline__ cx<double> widen(cx<T> a) {
+  return mk((double)a.r, (double)a.i);
+}
+template <class T>
+__device__ __forceinline__ cx<T> narrow(cx<double> a) {
+  return mk((T)a.r, (T)a.i);
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0;
+  if (threadIdx.x < 32) {
+    s = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  return s;  // valid in thread 0
+}
+
+// out[f] = sum_n |x[f][n]|^2 over instances with act[f] (one block per instance)
+template <class T>
+__global__ void norm2_kernel(const cx<T>* x, int64_t N, const int32_t* act, double* out) {
+  __shared__ double sh[32];
+  const int64_t f = blockIdx.x;
+  if (act && !act[f]) return;
+  const cx<T>* v = x + f * N;
+  double s = 0;
+  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
+    const cx<double> z = widen(v[n]);
+    s = fma(z.r, z.r, fma(z.i, z.i, s));
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[f] = s;
+}
+
+// dots[f][k] = sum_n conj(V[f][k][n]) w[f][n], k = 0..j  (grid: (j+1, F))
+template <class T>
+__global__ void gs_dots_kernel(const cx<T>* V, const cx<T>* w, int64_t N, int m1, int j,
+                               const int32_t* act, cx<double>* dots) {
+  __shared__ double sh[32];
+  const int k = blockIdx.x;
+  const int64_t f = blockIdx.y;
+  if (!act[f] || k > j) return;
+  const cx<T>* vk = V + (f * m1 + k) * N;
+  const cx<T>* wv = w + f * N;
+  double sr = 0, si = 0;
+  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
+    const cx<double> a = widen(vk[n]), b = widen(wv[n]);
+    sr = fma(a.r, b.r, fma(a.i, b.i, sr));
+    si = fma(a.r, b.i, fma(-a.i, b.r, si));
+  }
+  sr = block_sum(sr, sh);
+  si = block_sum(si, sh);
+  if (threadIdx.x == 0) dots[f * m1 + k] = mk(sr, si);
+}
+
+// w[f][n] -= sum_{k<=j} dots[f][k] V[f][k][n]; hacc[f][k] += dots[f][k] (grid: (nb, F))
+template <class T>
+__global__ void gs_update_kernel(const cx<T>* V, cx<T>* w, int64_t N, int m1, int j,
+                                 const int32_t* act, const cx<double>* dots, cx<double>* hacc) {
+  extern __shared__ cx<double> sd[];
+  const int64_t f = blockIdx.y;
+  if (!act[f]) return;
+  for (int k = threadIdx.x; k <= j; k += blockDim.x) sd[k] = dots[f * m1 + k];
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int k = threadIdx.x; k <= j; k += blockDim.x) hacc[f * m1 + k] = hacc[f * m1 + k] + sd[k];
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  cx<double> s = widen(w[f * N + n]);
+  for (int k = 0; k <= j; ++k) {
+    const cx<double> v = widen(V[(f * m1 + k) * N + n]);
+    s = s - sd[k] * v;
+  }
+  w[f * N + n] = narrow<T>(s);
+}
+
+struct GState {
+  cx<double>* H;      // [F][m1][m] column-major by j: H[f][j*m1 + k]
+  double* cs;         // [F][m]
+  cx<double>* sn;     // [F][m]
+  cx<double>* g;      // [F][m1]
+  cx<double>* hacc;   // [F][m1] current column accumulator
+  double* hnorm2;     // [F]
+  double* target;     // [F] absolute residual target of this inner solve
+  double* inv_h;      // [F] 1 / H[j+1][j]
+  int32_t* act;       // [F] active in the current cycle
+  int32_t* kcols;     // [F] Krylov columns used
+  int32_t* status;    // [F] 0 ok, BEM_ERR_BREAKDOWN
+  double* est;        // [F] residual estimate |g_{k}|
+  int32_t* nact;      // [1] number of active instances after the step
+};
+
+// Finish Arnoldi column j for every active instance: Givens rotations, residual estimate,
+// retirement (one thread per instance).
+__global__ void arnoldi_finish_kernel(GState s, int64_t F, int m, int j) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= F || !s.act[f]) return;
+  const int m1 = m + 1;
+  cx<double>* h = s.H + f * (int64_t)m1 * m + (int64_t)j * m1;
+  for (int k = 0; k <= j; ++k) h[k] = s.hacc[f * m1 + k];
+  const double hn = sqrt(s.hnorm2[f]);
+  h[j + 1] = mk(hn, 0.0);
+  // previous rotations
+  for (int k = 0; k < j; ++k) {
+    const double c = s.cs[f * m + k];
+    const cx<double> sk = s.sn[f * m + k];
+    const cx<double> a = h[k], b = h[k + 1];
+    h[k] = c * a + sk * b;
+    h[k + 1] = c * b - conj(sk) * a;
+  }
+  const cx<double> a = h[j];
+  const double aa = sqrt(a.r * a.r + a.i * a.i);
+  const double rho = sqrt(aa * aa + hn * hn);
+  double c;
+  cx<double> sj;
+  if (aa == 0.0) {
+    c = 0.0;
+    sj = mk(1.0, 0.0);
+    h[j] = mk(hn, 0.0);
+  } else {
+    c = aa / rho;
+    sj = mk(a.r / aa * hn / rho, a.i / aa * hn / rho);  // (a/|a|) conj(b) / rho, b = hn real
+    h[j] = mk(a.r / aa * rho, a.i / aa * rho);
+  }
+  h[j + 1] = mk(0.0, 0.0);
+  s.cs[f * m + j] = c;
+  s.sn[f * m + j] = sj;
+  const cx<double> gj = s.g[f * m1 + j];
+  s.g[f * m1 + j] = c * gj;
+  s.g[f * m1 + j + 1] = (-1.0) * (conj(sj) * gj);
+  const cx<double> gn = s.g[f * m1 + j + 1];
+  const double res = sqrt(gn.r * gn.r + gn.i * gn.i);
+  s.est[f] = res;
+  s.kcols[f] = j + 1;
+  const bool bad = !isfinite(res) || !isfinite(hn) || !isfinite(rho);
+  if (bad) s.status[f] = BEM_ERR_BREAKDOWN;
+  const bool done = bad || res <= s.target[f] || hn <= 1e-300 || j + 1 >= m;
+  s.inv_h[f] = hn > 1e-300 ? 1.0 / hn : 0.0;
+  if (done) s.act[f] = 0;
+  else atomicAdd(s.nact, 1);
+}
+
+template <class T>
+__global__ void normalize_kernel(const cx<T>* w, cx<T>* V, int64_t N, int m1, int j,
+                                 const int32_t* act, const double* inv_h) {
+  const int64_t f = blockIdx.y;
+  if (!act[f]) return;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const double s = inv_h[f];
+  const cx<double> v = widen(w[f * N + n]);
+  V[(f * m1 + j + 1) * N + n] = narrow<T>(s * v);
+}
+
+// v0 = r / ||r|| (to T), g = (beta, 0, ...), H accumulators cleared.
+template <class T>
+__global__ void start_kernel(const cx<double>* r, const double* rn2, cx<T>* V, int64_t N, int m1,
+                             const int32_t* act, cx<double>* g) {
+  const int64_t f = blockIdx.y;
+  if (!act[f]) return;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const double beta = sqrt(rn2[f]);
+  if (n < m1) g[f * m1 + n] = mk(n == 0 ? beta : 0.0, 0.0);
+  if (n >= N) return;
+  const double s = beta > 0 ? 1.0 / beta : 0.0;
+  V[f * m1 * N + n] = narrow<T>(s * r[f * N + n]);
+}
+
+__global__ void clear_hacc_kernel(cx<double>* hacc, int64_t F, int m1, const int32_t* act) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= F * m1) return;
+  if (act[t / m1]) hacc[t] = mk(0.0, 0.0);
+}
+
+// y = R^{-1} g on the first k columns (back substitution), per instance.
+__global__ void lsq_kernel(GState s, int64_t F, int m, const int32_t* part, cx<double>* y) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= F || !part[f]) return;
+  const int m1 = m + 1;
+  const int k = s.kcols[f];
+  const cx<double>* H = s.H + f * (int64_t)m1 * m;
+  cx<double>* yf = y + f * m1;
+  for (int r = k - 1; r >= 0; --r) {
+    cx<double> acc = s.g[f * m1 + r];
+    for (int c = r + 1; c < k; ++c) acc = acc - H[(int64_t)c * m1 + r] * yf[c];
+    const cx<double> d = H[(int64_t)r * m1 + r];
+    const double dd = d.r * d.r + d.i * d.i;
+    yf[r] = dd > 0 ? acc * mk(d.r / dd, -d.i / dd) : mk(0.0, 0.0);
+  }
+}
+
+// u[f] = sum_{k < kcols[f]} y[f][k] V[f][k]  (into T buffer)
+template <class T>
+__global__ void combine_kernel(const cx<T>* V, const cx<double>* y, const int32_t* kcols,
+                               int64_t N, int m1, const int32_t* part, cx<T>* u) {
+  const int64_t f = blockIdx.y;
+  if (!part[f]) return;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  cx<double> s = mk(0.0, 0.0);
+  const int k = kcols[f];
+  for (int c = 0; c < k; ++c) s = s + y[f * m1 + c] * widen(V[(f * m1 + c) * N + n]);
+  u[f * N + n] = narrow<T>(s);
+}
+
+// x64 += d (widened), for participating instances
+template <class T>
+__global__ void add_correction_kernel(cx<double>* x, const cx<T>* d, int64_t N, int64_t F,
+                                      const int32_t* part) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= F * N || !part[t / N]) return;
+  x[t] = x[t] + widen(d[t]);
+}
+
+// r = b - Ax  (for active instances)
+__global__ void residual_kernel(const cx<double>* b, const cx<double>* Ax, cx<double>* r,
+                                int64_t N, int64_t F, const int32_t* act) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= F * N || !act[t / N]) return;
+  r[t] = b[t] - Ax[t];
+}
+
+// ------------------------------------------------------------------------------- host driver
+namespace {
+
+struct Work {
+  cx<double>* x = nullptr;    // FP64 [F][N] solution (caller-owned)
+  DevBuf b, r, Ax;            // FP64 [F][N]
+  DevBuf V, z, w, u;          // T
+  DevBuf H, cs, sn, g, hacc, dots, y;
+  DevBuf hnorm2, target, inv_h, est, bn2, rn2;
+  DevBuf act, part, kcols, status, nact;
+};
+
+template <class T>
+struct Ops;
+template <>
+struct Ops<float> {
+  static void op(bem_ctx* c, const cx<float>* x, cx<float>* y, const int32_t* a) {
+    apply_operator32(c, x, y, BEM_APPLY_A, a);
+  }
+  static void pre(bem_ctx* c, const cx<float>* x, cx<float>* y, const int32_t* a) {
+    apply_precond32(c, x, y, a);
+  }
+};
+template <>
+struct Ops<double> {
+  static void op(bem_ctx* c, const cx<double>* x, cx<double>* y, const int32_t* a) {
+    apply_operator64(c, x, y, BEM_APPLY_A, a);
+  }
+  static void pre(bem_ctx* c, const cx<double>* x, cx<double>* y, const int32_t* a) {
+    apply_precond64(c, x, y, a);
+  }
+};
+
+// One GMRES(m) cycle on A M^{-1} y = r for the instances flagged in `part` (device), starting
+// from x = 0 of the correction; adds the correction to x64.  Returns iterations performed.
+template <class T>
+int gmres_cycle(bem_ctx* ctx, Work& W, int64_t F, int64_t N, int m,
+                std::vector<int32_t>& iters_host) {
+  cudaStream_t st = ctx->stream;
+  const int m1 = m + 1;
+  GState s;
+  s.H = W.H.as<cx<double>>();
+  s.cs = W.cs.as<double>();
+  s.sn = W.sn.as<cx<double>>();
+  s.g = W.g.as<cx<double>>();
+  s.hacc = W.hacc.as<cx<double>>();
+  s.hnorm2 = W.hnorm2.as<double>();
+  s.target = W.target.as<double>();
+  s.inv_h = W.inv_h.as<double>();
+  s.act = W.act.as<int32_t>();
+  s.kcols = W.kcols.as<int32_t>();
+  s.status = W.status.as<int32_t>();
+  s.est = W.est.as<double>();
+  s.nact = W.nact.as<int32_t>();
+  cx<T>* V = W.V.as<cx<T>>();
+  cx<T>* z = W.z.as<cx<T>>();
+  cx<T>* w = W.w.as<cx<T>>();
+  const int32_t* part = W.part.as<int32_t>();
+  int32_t* act = W.act.as<int32_t>();
+  BEM_CUDA(cudaMemcpyAsync(act, part, sizeof(int32_t) * F, cudaMemcpyDeviceToDevice, st));
+  BEM_CUDA(cudaMemsetAsync(s.kcols, 0, sizeof(int32_t) * F, st));
+  const dim3 gv(grid_for(N, 256), (unsigned)F);
+  start_kernel<T><<<dim3(grid_for(std::max<int64_t>(N, m1), 256), (unsigned)F), 256, 0, st>>>(
+      W.r.as<cx<double>>(), W.rn2.as<double>(), V, N, m1, act, s.g);
+  BEM_LAUNCHED();
+  ctx->launches++;
+  std::vector<int32_t> act_h(F);
+  int it = 0;
+  for (int j = 0; j < m; ++j) {
+    // z = M^{-1} v_j: column j of V is strided by m1 N, gather it into w first
+    BEM_CUDA(cudaMemcpy2DAsync(w, sizeof(cx<T>) * N, V + (size_t)j * N, sizeof(cx<T>) * N * m1,
+                               sizeof(cx<T>) * N, F, cudaMemcpyDeviceToDevice, st));
+    Ops<T>::pre(ctx, w, z, act);
+    Ops<T>::op(ctx, z, w, act);
+    clear_hacc_kernel<<<grid_for(F * m1, 256), 256, 0, st>>>(s.hacc, F, m1, act);
+    ctx->launches++;
+    for (int pass = 0; pass < 2; ++pass) {
+      gs_dots_kernel<T><<<dim3(j + 1, (unsigned)F), 256, 0, st>>>(V, w, N, m1, j, act,
+                                                                 W.dots.as<cx<double>>());
+      ctx->launches++;
+      gs_update_kernel<T><<<gv, 256, sizeof(cx<double>) * m1, st>>>(
+          V, w, N, m1, j, act, W.dots.as<cx<double>>(), s.hacc);
+      ctx->launches++;
+    }
+    norm2_kernel<T><<<(unsigned)F, 256, 0, st>>>(w, N, act, s.hnorm2);
+    ctx->launches++;
+    BEM_CUDA(cudaMemsetAsync(s.nact, 0, sizeof(int32_t), st));
+    arnoldi_finish_kernel<<<grid_for(F, 128), 128, 0, st>>>(s, F, m, j);
+    ctx->launches++;
+    normalize_kernel<T><<<gv, 256, 0, st>>>(w, V, N, m1, j, act, s.inv_h);
+    ctx->launches++;
+    BEM_LAUNCHED();
+    int32_t nact = 0;
+    BEM_CUDA(cudaMemcpyAsync(&nact, s.nact, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    BEM_CUDA(cudaStreamSynchronize(st));
+    ++it;
+    if (nact == 0) break;
+  }
+  // update: x += M^{-1} V y
+  lsq_kernel<<<grid_for(F, 128), 128, 0, st>>>(s, F, m, part, W.y.as<cx<double>>());
+  combine_kernel<T><<<gv, 256, 0, st>>>(V, W.y.as<cx<double>>(), s.kcols, N, m1, part, w);
+  Ops<T>::pre(ctx, w, z, part);
+  add_correction_kernel<T><<<grid_for(F * N, 256), 256, 0, st>>>(W.x, z, N, F, part);
+  ctx->launches += 3;
+  BEM_LAUNCHED();
+  std::vector<int32_t> kc(F), ph(F);
+  BEM_CUDA(cudaMemcpyAsync(kc.data(), s.kcols, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, st));
+  BEM_CUDA(cudaMemcpyAsync(ph.data(), part, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, st));
+  BEM_CUDA(cudaStreamSynchronize(st));
+  for (int64_t f = 0; f < F; ++f)
+    if (ph[f]) iters_host[f] += kc[f];
+  return it;
+}
+
+template <class T>
+void reserve_inner(Work& W, int64_t F, int64_t N, int m) {
+  const int m1 = m + 1;
+  W.V.reserve(sizeof(cx<T>) * F * m1 * N);
+  W.z.reserve(sizeof(cx<T>) * F * N);
+  W.w.reserve(sizeof(cx<T>) * F * N);
+}
+
+}  // namespace
+
+void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
+                 std::vector<int32_t>& iters, std::vector<int32_t>& refines,
+                 std::vector<double>& resid, std::vector<int32_t>& status) {
+  const int64_t F = ctx->fs.F, N = 3 * ctx->mesh.ne;
+  const bem_options& o = ctx->opt;
+  const int m = std::max(1, o.restart);
+  const int m1 = m + 1;
+  const bool mixed = o.precision == BEM_PREC_MIXED;
+  cudaStream_t st = ctx->stream;
+  Work W;
+  W.b.reserve(sizeof(cx<double>) * F * N);
+  W.r.reserve(sizeof(cx<double>) * F * N);
+  W.Ax.reserve(sizeof(cx<double>) * F * N);
+  W.x = x_dev;
+  if (mixed) reserve_inner<float>(W, F, N, m);
+  else reserve_inner<double>(W, F, N, m);
+  W.H.reserve(sizeof(cx<double>) * F * m1 * m);
+  W.cs.reserve(sizeof(double) * F * m);
+  W.sn.reserve(sizeof(cx<double>) * F * m);
+  W.g.reserve(sizeof(cx<double>) * F * m1);
+  W.hacc.reserve(sizeof(cx<double>) * F * m1);
+  W.dots.reserve(sizeof(cx<double>) * F * m1);
+  W.y.reserve(sizeof(cx<double>) * F * m1);
+  for (DevBuf* b : {&W.hnorm2, &W.target, &W.inv_h, &W.est, &W.bn2, &W.rn2}) b->reserve(sizeof(double) * F);
+  for (DevBuf* b : {&W.act, &W.part, &W.kcols, &W.status}) b->reserve(sizeof(int32_t) * F);
+  W.nact.reserve(sizeof(int32_t));
+  BEM_CUDA(cudaMemsetAsync(W.status.p, 0, sizeof(int32_t) * F, st));
+
+  // b = K (profile * data) in FP64
+  known_data(ctx, W.Ax.as<cx<double>>());
+  apply_operator64(ctx, W.Ax.as<cx<double>>(), W.b.as<cx<double>>(), BEM_APPLY_K, nullptr);
+  norm2_kernel<double><<<(unsigned)F, 256, 0, st>>>(W.b.as<cx<double>>(), N, nullptr, W.bn2.as<double>());
+  ctx->launches++;
+  // x = 0, r = b
+  BEM_CUDA(cudaMemsetAsync(x_dev, 0, sizeof(cx<double>) * F * N, st));
+  BEM_CUDA(cudaMemcpyAsync(W.r.p, W.b.p, sizeof(cx<double>) * F * N, cudaMemcpyDeviceToDevice, st));
+  BEM_CUDA(cudaMemcpyAsync(W.rn2.p, W.bn2.p, sizeof(double) * F, cudaMemcpyDeviceToDevice, st));
+  std::vector<double> bn2(F), rn2(F), est(F), tgt(F);
+  std::vector<int32_t> part(F, 1), stat(F);
+  BEM_CUDA(cudaMemcpyAsync(bn2.data(), W.bn2.p, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
+  BEM_CUDA(cudaStreamSynchronize(st));
+  rn2 = bn2;
+  iters.assign(F, 0);
+  refines.assign(F, 0);
+  resid.assign(F, 1.0);
+  status.assign(F, BEM_ERR_NOT_CONVERGED);
+  std::vector<char> done(F, 0);
+  for (int64_t f = 0; f < F; ++f)
+    if (bn2[f] == 0.0) {  // zero right-hand side: x = 0 is exact
+      done[f] = 1;
+      resid[f] = 0.0;
+      status[f] = 0;
+    }
+  const int max_outer = mixed ? std::max(1, o.max_refine) : std::max(1, o.max_iters / m + 1);
+  int total_inner = 0;
+  for (int outer = 0; outer < max_outer; ++outer) {
+    // who still needs work
+    int64_t nwork = 0;
+    for (int64_t f = 0; f < F; ++f) {
+      part[f] = done[f] ? 0 : 1;
+      nwork += part[f];
+      const double rn = std::sqrt(rn2[f]), bnrm = std::sqrt(bn2[f]);
+      tgt[f] = mixed ? std::max(o.inner_tol * rn, 0.25 * o.tol * bnrm) : 0.999 * o.tol * bnrm;
+    }
+    if (nwork == 0) break;
+    if (total_inner >= o.max_iters) break;
+    BEM_CUDA(cudaMemcpyAsync(W.part.p, part.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
+    BEM_CUDA(cudaMemcpyAsync(W.target.p, tgt.data(), sizeof(double) * F, cudaMemcpyHostToDevice, st));
+    int it = mixed ? gmres_cycle<float>(ctx, W, F, N, m, iters) : gmres_cycle<double>(ctx, W, F, N, m, iters);
+    total_inner += it;
+    BEM_CUDA(cudaMemcpyAsync(est.data(), W.est.p, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
+    BEM_CUDA(cudaMemcpyAsync(stat.data(), W.status.p, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, st));
+    BEM_CUDA(cudaStreamSynchronize(st));
+    for (int64_t f = 0; f < F; ++f)
+      if (part[f] && stat[f] == BEM_ERR_BREAKDOWN) {
+        done[f] = 1;
+        part[f] = 0;
+        status[f] = BEM_ERR_BREAKDOWN;
+      }
+    if (!mixed) {
+      // plain FP64: accept the FP64 GMRES residual estimate when it meets the tolerance;
+      // otherwise restart from the true residual.
+      bool need_restart = false;
+      for (int64_t f = 0; f < F; ++f) {
+        if (!part[f]) continue;
+        const double rel = est[f] / std::sqrt(bn2[f]);
+        if (est[f] <= o.tol * std::sqrt(bn2[f])) {
+          done[f] = 1;
+          part[f] = 0;
+          resid[f] = rel;
+          status[f] = 0;
+        } else {
+          need_restart = true;
+          resid[f] = rel;
+        }
+      }
+      if (!need_restart) break;
+    }
+    // FP64 residual r = b - A x for the instances still working
+    BEM_CUDA(cudaMemcpyAsync(W.part.p, part.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
+    int64_t any = 0;
+    for (int64_t f = 0; f < F; ++f) any += part[f];
+    if (!any) break;
+    apply_operator64(ctx, x_dev, W.Ax.as<cx<double>>(), BEM_APPLY_A, W.part.as<int32_t>());
+    residual_kernel<<<grid_for(F * N, 256), 256, 0, st>>>(W.b.as<cx<double>>(), W.Ax.as<cx<double>>(),
+                                                          W.r.as<cx<double>>(), N, F, W.part.as<int32_t>());
+    norm2_kernel<double><<<(unsigned)F, 256, 0, st>>>(W.r.as<cx<double>>(), N, W.part.as<int32_t>(),
+                                                      W.rn2.as<double>());
+    ctx->launches += 2;
+    BEM_LAUNCHED();
+    BEM_CUDA(cudaMemcpyAsync(rn2.data(), W.rn2.p, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
+    BEM_CUDA(cudaStreamSynchronize(st));
+    for (int64_t f = 0; f < F; ++f) {
+      if (!part[f]) continue;
+      refines[f]++;
+      const double rel = std::sqrt(rn2[f] / bn2[f]);
+      resid[f] = rel;
+      if (!std::isfinite(rel)) {
+        done[f] = 1;
+        status[f] = BEM_ERR_BREAKDOWN;
+      } else if (rel <= o.tol) {
+        done[f] = 1;
+        status[f] = 0;
+      }
+    }
+  }
+}
+
+}  // namespace bem

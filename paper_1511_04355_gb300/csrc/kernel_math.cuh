@@ -1,0 +1,104 @@
+// Device arithmetic of the Laplace-domain elastodynamic fundamental solutions.
+//
+// The boundary integral equation (Sec. 2.1, Eq. (bie)) uses the displacement and traction
+// fundamental solutions U_ij, T_ij of the Laplace-transformed Navier equation (the paper omits
+// them as textbook material).  With r = y - x, r = |r|, rh = r / r, n the unit normal at y,
+// z = s r / c_s, beta = c_s / c_p, E_s = e^{-z}, E_p = e^{-beta z}, g_s = (1 + z) E_s,
+// g_p = (1 + beta z) E_p and
+//     J = (g_p - g_s) / z^2            (= beta^2 h(beta z) - h(z), h(z) = ((1+z)e^{-z} - 1)/z^2),
+// the kernels reduce to
+//     4 pi mu r U_ij = (E_s - J) delta_ij - (P - 3 J) rh_i rh_j,     P = E_s - beta^2 E_p,
+//     4 pi r^2 T_ij  = A (delta_ij dr/dn + n_i rh_j) + q1 rh_i n_j + q2 dr/dn rh_i rh_j,
+//     Q = 6 J - 2 P,  A = Q - g_s,  q1 = Q - (1 - 2 beta^2) g_p,  q2 = 2 (g_s - beta^2 g_p) - 5 Q.
+// (Static limit z -> 0: A -> -beta^2, q1 -> beta^2, q2 -> -3 (1 - beta^2): Kelvin's kernels.)
+// J cancels catastrophically for small |z|; there its Taylor series
+//     J = sum_m d_m z^m,  d_m = c_{m+2} (beta^{m+2} - 1),  c_n = (-1)^n (1 - n) / n!,
+// is used (|z|^2 < 1/4; 9 terms in FP32, 18 in FP64).
+#pragma once
+
+#include "bem_internal.cuh"
+
+namespace bem {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kInv4Pi = 0.07957747154594767;
+
+// e^{-z} for complex z, FP32: amplitude by the exp unit, phase reduced to [-pi, pi] by a
+// two-constant Cody-Waite split of 2 pi before the hardware sine/cosine.
+__device__ __forceinline__ cx<float> exp_neg(cx<float> z) {
+  const float amp = __expf(-z.r);
+  const float k = rintf(z.i * 0.159154943091895336f);
+  float red = fmaf(-k, 6.28318548202514648f, z.i);     // 2 pi rounded to float
+  red = fmaf(-k, -1.74845560007440834e-07f, red);      // 2 pi - (2 pi rounded to float)
+  float sn, cs;
+  __sincosf(red, &sn, &cs);
+  return mk(amp * cs, -amp * sn);
+}
+
+// e^{-z} for complex z, FP64 (library exp and sincos).
+__device__ __forceinline__ cx<double> exp_neg(cx<double> z) {
+  const double amp = exp(-z.r);
+  double sn, cs;
+  sincos(z.i, &sn, &cs);
+  return mk(amp * cs, -amp * sn);
+}
+
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+
+template <class R>
+struct NSeries;
+template <>
+struct NSeries<float> {
+  static constexpr int n = kSeriesF32;
+};
+template <>
+struct NSeries<double> {
+  static constexpr int n = kSeriesF64;
+};
+
+// Radial part shared by U and T: E_s, P = E_s - beta^2 E_p, J, g_s, g_p at distance r.
+template <class R>
+struct Radial {
+  cx<R> Es, P, J, gs, gp;
+};
+
+template <class R>
+__device__ __forceinline__ Radial<R> radial(R r, R inv_r2, const FreqC<R>& fc, const MatC<R>& m) {
+  Radial<R> o;
+  const cx<R> zs = r * fc.a;
+  const cx<R> zp = m.beta * zs;
+  o.Es = exp_neg(zs);
+  const cx<R> Ep = exp_neg(zp);
+  o.gs = cfma(zs, o.Es, o.Es);
+  o.gp = cfma(zp, Ep, Ep);
+  o.P = axpy(-m.beta2, Ep, o.Es);
+  const R z2 = r * r * fc.a_abs2;
+  if (z2 < R(kZSeries2)) {
+    constexpr int NS = NSeries<R>::n;
+    cx<R> acc = mk(m.d[NS - 1], R(0));
+#pragma unroll
+    for (int k = NS - 2; k >= 0; --k) acc = cfma(acc, zs, mk(m.d[k], R(0)));
+    o.J = acc;
+  } else {
+    o.J = inv_r2 * ((o.gp - o.gs) * fc.inv_a2);
+  }
+  return o;
+}
+
+// T coefficients (times 4 pi r^2): A, q1, q2.
+template <class R>
+struct TCoef {
+  cx<R> A, q1, q2;
+};
+template <class R>
+__device__ __forceinline__ TCoef<R> tcoef(const Radial<R>& k, const MatC<R>& m) {
+  TCoef<R> t;
+  const cx<R> Q = axpy(R(-2), k.P, R(6) * k.J);
+  t.A = Q - k.gs;
+  t.q1 = axpy(-m.c1m2b2, k.gp, Q);
+  t.q2 = axpy(R(-5), Q, R(2) * axpy(-m.beta2, k.gp, k.gs));
+  return t;
+}
+
+}  // namespace bem
