@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark: converged Laplace-domain BEM frequency solves per second on GB300.
+
+Workload (one "step" = one batched solve of every frequency): pressurised spherical cavity in a
+full space, icosphere of radius 1 m with 5120 flat triangles (15360 complex unknowns),
+mu = 1e9 Pa, nu = 0.25, rho = 2000 kg/m^3, step pressure 1e6 Pa, the 128 frequencies
+s_k = 250 + i k pi / 0.02 (k = 0..127), GMRES(50) to ||b - A x|| / ||b|| <= 1e-6 measured in
+FP64, FP32 matrix-free operator with FP64 iterative refinement.
+
+value : solves/s with the frequency list, the mesh and the output already in device memory.
+e2e   : the same through the C ABI with host buffers (mesh, boundary data and frequencies
+        uploaded, all solutions downloaded, every step).
+Also reported: the plain-FP64 GPU path on a 16-frequency sample, the per-kernel roofline of the
+dominant kernel (CUDA events around each launch on the launching stream), SM clocks sampled
+during the timed region, and the FP64 CPU oracle on a bounded sample (cpu_baseline).
+
+--impl reference times the CPU oracle (dense assembly + LU, FP64) on the same workload: each
+step is a bounded sample (a block of matrix rows at one frequency plus an LU of a smaller dense
+system), extrapolated to one full solve.
+Multi-GPU (torchrun, N ranks): every rank solves its own 128 frequencies of an N*128 frequency
+grid (weak scaling, no collective on the data path); value = all solves / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+LEVEL = 4            # 5120 triangles
+N_FREQ = 128
+T_WIN = 0.02
+SIGMA = 250.0
+TOL = 1e-6
+FP64_SAMPLE = 16     # frequencies of the plain-FP64 comparison (every 8th)
+METRIC = "BEM frequency solves/s at 1e-6 rel. residual vs plain FP64 GPU; % FP32 peak"
+# FP32 far-field kernel, traction columns: FP32 flops per kernel evaluation counted from the
+# kernel source (FMA = 2; exp/sin/cos on the special-function unit not counted)
+FLOPS_PER_UNIT_T = 159
+FLOPS_PER_UNIT_U = 113   # displacement-kernel (U) columns: the right-hand side pass
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def workload_config(n_gpus):
+    return {
+        "workload": "pressurised spherical cavity, icosphere 5120 flat triangles (15360 complex "
+                    "unknowns), 128 frequencies s_k=250+i*k*pi/0.02, GMRES(50) to 1e-6 FP64 "
+                    "residual, FP32 operator + FP64 refinement",
+        "n_triangles": 20 * 4 ** LEVEL, "n_unknowns": 3 * 20 * 4 ** LEVEL,
+        "n_freq_per_gpu": N_FREQ, "tol": TOL, "restart": 50,
+        "l2": "flushed between timed steps (256 MiB device write)",
+        "parallelism": f"frequency shards x{n_gpus}" if n_gpus > 1 else "single GPU",
+    }
+
+
+# ------------------------------------------------------------------------------ helpers
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+def oracle_sample(rows=128, n_lu=3072, seed=0):
+    """Oracle cost of one full solve of the workload, from a bounded sample: dense assembly of
+    `rows` matrix block-rows at one mid-band frequency, and an LU solve of an n_lu dense complex
+    system; extrapolated by 5120/rows (assembly) and (15360/n_lu)^3 (LU)."""
+    from oracle import bem as OB
+
+    prob = W.spherical_cavity(level=LEVEL, n_freq=N_FREQ, T=T_WIN, sigma=SIGMA)
+    g = OB.geometry(prob.verts, prob.tris)
+    ne = len(prob.tris)
+    sel = np.linspace(0, ne - 1, rows).astype(int)
+    t0 = time.perf_counter()
+    OB.operators(g, prob.s[64], prob.material, prob.bc_type, rows=sel)
+    t_asm = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n_lu, n_lu)) + 1j * rng.standard_normal((n_lu, n_lu))
+    b = rng.standard_normal(n_lu) + 0j
+    t0 = time.perf_counter()
+    np.linalg.solve(A, b)
+    t_lu = time.perf_counter() - t0
+    per_solve = t_asm * ne / rows + t_lu * (3 * ne / n_lu) ** 3
+    sample = (f"dense assembly of {rows} of {ne} block-rows at s_64 ({t_asm:.2f} s, x{ne / rows:.0f}) "
+              f"+ LU of a {n_lu}^2 complex system ({t_lu:.2f} s, x{(3 * ne / n_lu) ** 3:.0f}); "
+              f"extrapolated {per_solve:.0f} s per solve")
+    return 1.0 / per_solve, sample, t_asm + t_lu
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cores = os.cpu_count()
+    for _ in range(args.warmup):
+        oracle_sample()
+    vals, walls = [], []
+    for _ in range(args.steps):
+        v, sample, wall = oracle_sample()
+        vals.append(v)
+        walls.append(wall)
+    value = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.gpus),
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "sample_wall_s": float(np.median(walls)),
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ GPU
+def run_gpu(args):
+    import torch
+
+    import paper_1511_04355_gb300 as P
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    prob = W.spherical_cavity(level=LEVEL, n_freq=N_FREQ * ws, T=T_WIN, sigma=SIGMA)
+    s_all = prob.s[rank * N_FREQ:(rank + 1) * N_FREQ]
+    ne = len(prob.tris)
+    n_unk = 3 * ne
+    m = prob.material
+
+    ctx = P.Context(local, stream.cuda_stream)
+    ctx.set_mesh(prob.verts, prob.tris)
+    ctx.set_material(m.mu, m.nu, m.rho)
+    ctx.set_bc(prob.bc_type, prob.bc_value, P.BEM_PROFILE_STEP)
+    ctx.set_options(precision=P.BEM_PREC_MIXED, tol=TOL)
+
+    s_dev = torch.from_numpy(np.ascontiguousarray(s_all)).to(dev)
+    x_dev = torch.zeros((N_FREQ, n_unk), dtype=torch.complex128, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def step():
+        _, info = P.bem_solve_frequencies(ctx.h, s_dev, x_dev)
+        return info
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    # timed region: device-resident inputs
+    launches = 0
+    times = []
+    infos = []
+    ctx.profile(True)
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = step()
+            e1.record(stream)
+            barrier()
+            times.append(e0.elapsed_time(e1))
+            launches += int(info["kernel_launches"])
+            infos.append(info)
+    ktimes = ctx.kernel_times()
+    ctx.profile(False)
+    t_step = float(np.mean(times))
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = ws * N_FREQ / (t_step / 1e3)
+
+    # e2e through the ABI with host buffers (pinned), every step uploads mesh, data, s and
+    # downloads all solutions
+    verts = np.ascontiguousarray(prob.verts)
+    tris = np.ascontiguousarray(prob.tris, dtype=np.int32)
+    x_host_t = torch.empty((N_FREQ, n_unk), dtype=torch.complex128, pin_memory=True)
+    x_host = x_host_t.numpy()
+    s_host = np.ascontiguousarray(s_all)
+    h2d = verts.nbytes + tris.nbytes + prob.bc_type.nbytes + prob.bc_value.nbytes + s_host.nbytes
+    d2h = x_host.nbytes
+
+    def e2e_step():
+        P.bem_set_mesh(ctx.h, verts, tris)
+        P.bem_set_material(ctx.h, m.mu, m.nu, m.rho)
+        P.bem_set_bc(ctx.h, prob.bc_type, prob.bc_value, P.BEM_PROFILE_STEP)
+        P.bem_solve_frequencies(ctx.h, s_host, x_host)
+
+    e2e_step()
+    et = []
+    for _ in range(args.steps):
+        flush.zero_()
+        barrier()
+        t0 = time.perf_counter()
+        e2e_step()
+        barrier()
+        et.append(time.perf_counter() - t0)
+    t_e2e = float(np.mean(et))
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e_value = ws * N_FREQ / t_e2e
+
+    # accuracy and the plain-FP64 GPU path on a sample of the band
+    sel = np.arange(0, N_FREQ, N_FREQ // FP64_SAMPLE)
+    x_mixed = x_dev[sel].cpu().numpy()
+    ctx.set_options(precision=P.BEM_PREC_FP64, tol=TOL)
+    s64 = torch.from_numpy(np.ascontiguousarray(s_all[sel])).to(dev)
+    x64 = torch.zeros((len(sel), n_unk), dtype=torch.complex128, device=dev)
+    P.bem_solve_frequencies(ctx.h, s64, x64)        # warm-up of the FP64 path
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, info64 = P.bem_solve_frequencies(ctx.h, s64, x64)
+    e1.record(stream)
+    barrier()
+    t64 = e0.elapsed_time(e1) / 1e3
+    fp64_value = len(sel) / t64
+    # the same sample through the mixed path, for a like-for-like ratio
+    ctx.set_options(precision=P.BEM_PREC_MIXED, tol=TOL)
+    xm = torch.zeros_like(x64)
+    barrier()
+    e0.record(stream)
+    P.bem_solve_frequencies(ctx.h, s64, xm)
+    e1.record(stream)
+    barrier()
+    tm = e0.elapsed_time(e1) / 1e3
+    x64h = x64.cpu().numpy()
+    err = np.linalg.norm(x_mixed - x64h, axis=1) / np.linalg.norm(x64h, axis=1)
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel class (device time summed over the timed steps)
+    clocks = clk.summary()
+    per_step = {k: (n / args.steps, ms / args.steps) for k, (n, ms) in ktimes.items()}
+    dominant = max(ktimes, key=lambda k: ktimes[k][1])
+    info = infos[-1]
+    # FP32 far kernel units: every launch covers (ne^2 - ne) x 4 source points x active freqs;
+    # the number of frequency-launches is the iteration count summed over frequencies
+    f32_freq_launches = int(np.sum(info["iterations"]))
+    units32 = f32_freq_launches * (ne * ne - ne) * 4
+    n32, ms32 = per_step["far32"]
+    peak32 = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    ach32 = units32 * FLOPS_PER_UNIT_T / (ms32 / 1e3) / 1e12 if ms32 > 0 else 0.0
+    # FP64 far kernel: the RHS pass (U columns, every frequency) + one T pass per refinement
+    flops64 = (N_FREQ * FLOPS_PER_UNIT_U + int(np.sum(info["refinements"])) * FLOPS_PER_UNIT_T) \
+        * (ne * ne - ne) * 4
+    n64, ms64 = per_step["far64"]
+    ach64 = flops64 / (ms64 / 1e3) / 1e12 if ms64 > 0 else 0.0
+    roof32 = {"kernel": "far_kernel<float> (FP32 far-field operator)", "bound": "alu",
+              "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
+              "traffic": None, "launches_per_step": n32, "ms_per_step": ms32,
+              "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (recipe unit counts, max clock)"}
+    roof64 = {"kernel": "far_kernel<double> (FP64 far-field operator: RHS and refinement residuals)",
+              "bound": "alu", "achieved": ach64, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+              "frac": ach64 / FP64_NOMINAL_TFLOPS, "traffic": None, "launches_per_step": n64,
+              "ms_per_step": ms64, "peak_note": "nominal GB300 FP64 1.25 TFLOP/s (recipe table)"}
+    roofline = roof64 if dominant == "far64" else roof32
+
+    cpu_v, cpu_sample, _ = (None, None, None)
+    if ws == 1 and not args.skip_cpu:
+        cpu_v, cpu_sample, _ = oracle_sample()
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic", "config": workload_config(ws),
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "roofline": roofline,
+        "roofline_fp32_operator": roof32,
+        "kernel_ms_per_step": {k: v[1] for k, v in per_step.items()},
+        "fp64_gpu_path": {"value": fp64_value, "unit": "solves/s",
+                          "sample": f"{len(sel)} of the {N_FREQ} frequencies (every {N_FREQ // len(sel)}th)",
+                          "mixed_same_sample": len(sel) / tm,
+                          "speedup_mixed_vs_fp64": (len(sel) / tm) / fp64_value,
+                          "iterations": info64["iterations"].tolist()},
+        "accuracy": {"max_fp64_residual": float(np.max(info["residual"])),
+                     "max_rel_err_vs_fp64_gpu_path": float(err.max()),
+                     "iterations": info["iterations"].tolist(),
+                     "refinements": info["refinements"].tolist()},
+    }
+    if cpu_v is not None:
+        line["cpu_baseline"] = {"value": cpu_v, "unit": "solves/s", "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": cpu_sample}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -176,6 +176,24 @@ int bem_rhs(bem_ctx* ctx, const double* s, int64_t ns, double* b_out);
  * blocks A_ii(s_k) (free term + own-element integral).  FP64.  x, y: ns x 3ne complex. */
 int bem_precond_apply(bem_ctx* ctx, const double* s, int64_t ns, const double* x, double* y);
 
+/* ------------------------------------------------------------------ measurement */
+
+/* Kernel classes timed by bem_profile. */
+#define BEM_KERNEL_FAR32 0   /* FP32 far-field operator kernel (the hot loop)      */
+#define BEM_KERNEL_FAR64 1   /* FP64 far-field operator kernel (RHS, residuals)     */
+#define BEM_KERNEL_NEAR32 2  /* FP32 near-field + own-element correction          */
+#define BEM_KERNEL_NEAR64 3  /* FP64 near-field + own-element correction          */
+#define BEM_KERNEL_SELF 4    /* own-element singular blocks + preconditioner       */
+#define BEM_KERNEL_VEC 5     /* GMRES vector kernels of one Arnoldi step            */
+
+/* Enable (1) or disable (0) CUDA-event timing of the kernel classes above, on the context's
+ * stream; resets the totals.  Timing adds two event records per timed launch. */
+int bem_profile(bem_ctx* ctx, int enable);
+
+/* Totals since bem_profile(ctx, 1): number of timed launches and summed device milliseconds
+ * (events bracket each launch on the launching stream).  Errors: INVALID_ARG (bad kind). */
+int bem_kernel_time(bem_ctx* ctx, int kind, int64_t* launches, double* ms);
+
 #ifdef __cplusplus
 }
 #endif

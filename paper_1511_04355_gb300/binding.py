@@ -36,6 +36,13 @@ BEM_APPLY_K = 1
 BEM_WARM_ZERO = 0
 BEM_WARM_NEAREST = 1
 BEM_WARM_MLP = 2
+BEM_KERNEL_FAR32 = 0
+BEM_KERNEL_FAR64 = 1
+BEM_KERNEL_NEAR32 = 2
+BEM_KERNEL_NEAR64 = 3
+BEM_KERNEL_SELF = 4
+BEM_KERNEL_VEC = 5
+KERNEL_NAMES = {0: "far32", 1: "far64", 2: "near32", 3: "near64", 4: "self", 5: "gmres_vec"}
 
 
 class BemError(RuntimeError):
@@ -76,6 +83,8 @@ _SIGS = {
     "bem_apply": (C.c_int, [_P, _P, _I64, _P, _P, C.c_int, C.c_int]),
     "bem_rhs": (C.c_int, [_P, _P, _I64, _P]),
     "bem_precond_apply": (C.c_int, [_P, _P, _I64, _P, _P]),
+    "bem_profile": (C.c_int, [_P, C.c_int]),
+    "bem_kernel_time": (C.c_int, [_P, C.c_int, C.POINTER(_I64), C.POINTER(C.c_double)]),
 }
 
 _lib = None
@@ -125,6 +134,12 @@ def _check(ctx, rc, what):
 
 
 def _cplx_as_pairs(s):
+    """Frequency list as interleaved doubles: numpy (host) or a complex128 torch tensor (any
+    device, passed by pointer)."""
+    if hasattr(s, "data_ptr"):
+        if str(s.dtype) != "torch.complex128" or not s.is_contiguous():
+            raise TypeError("frequency tensors must be contiguous complex128")
+        return s, s.numel()
     s = np.ascontiguousarray(np.asarray(s, dtype=np.complex128).reshape(-1))
     return s, len(s)
 
@@ -247,6 +262,17 @@ def bem_precond_apply(ctx, s, x, y=None):
     return y
 
 
+def bem_profile(ctx, enable=True):
+    _check(ctx, load_library().bem_profile(ctx, 1 if enable else 0), "bem_profile")
+
+
+def bem_kernel_time(ctx, kind):
+    n = _I64()
+    ms = C.c_double()
+    _check(ctx, load_library().bem_kernel_time(ctx, kind, C.byref(n), C.byref(ms)), "bem_kernel_time")
+    return n.value, ms.value
+
+
 class Context:
     """Owns one bem_ctx (device + stream) and remembers the mesh size."""
 
@@ -296,6 +322,13 @@ class Context:
 
     def precond(self, s, x):
         return bem_precond_apply(self.h, s, x)
+
+    def profile(self, enable=True):
+        bem_profile(self.h, enable)
+
+    def kernel_times(self):
+        """{name: (launches, milliseconds)} since profile(True)."""
+        return {name: bem_kernel_time(self.h, k) for k, name in KERNEL_NAMES.items()}
 
     def geometry(self):
         return bem_geometry(self.h, self.ne)

@@ -30,6 +30,44 @@ void copy_out(bem_ctx* ctx, void* dst, const void* src, size_t bytes) {
   BEM_CUDA(cudaStreamSynchronize(ctx->stream));
 }
 
+static cudaEvent_t prof_event(bem_ctx* c) {
+  if (!c->prof_pool.empty()) {
+    cudaEvent_t e = c->prof_pool.back();
+    c->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  BEM_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+ProfScope::ProfScope(bem_ctx* ctx, int k) : c(ctx), kind(k) {
+  if (!c->prof) return;
+  a = prof_event(c);
+  b = prof_event(c);
+  cudaEventRecord(a, c->stream);
+}
+
+ProfScope::~ProfScope() {
+  if (!c->prof || !a) return;
+  cudaEventRecord(b, c->stream);
+  c->prof_recs.push_back(ProfRec{kind, a, b});
+}
+
+void prof_collect(bem_ctx* c) {
+  for (const ProfRec& r : c->prof_recs) {
+    float ms = 0;
+    cudaEventSynchronize(r.b);
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      c->prof_ms[r.kind] += ms;
+      c->prof_n[r.kind] += 1;
+    }
+    c->prof_pool.push_back(r.a);
+    c->prof_pool.push_back(r.b);
+  }
+  c->prof_recs.clear();
+}
+
 __global__ void narrow_kernel(const cx<double>* a, cx<float>* b, int64_t n) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t < n) b[t] = mk((float)a[t].r, (float)a[t].i);
@@ -119,10 +157,32 @@ int bem_create(bem_ctx** out, int device, void* stream) {
   }
 }
 
+int bem_profile(bem_ctx* ctx, int enable) {
+  return guarded(ctx, [&] {
+    prof_collect(ctx);
+    ctx->prof = enable != 0;
+    for (int k = 0; k < PK_COUNT; ++k) {
+      ctx->prof_ms[k] = 0;
+      ctx->prof_n[k] = 0;
+    }
+  });
+}
+
+int bem_kernel_time(bem_ctx* ctx, int kind, int64_t* launches, double* ms) {
+  return guarded(ctx, [&] {
+    BEM_REQUIRE(kind >= 0 && kind < PK_COUNT, "unknown kernel class");
+    prof_collect(ctx);
+    if (launches) *launches = ctx->prof_n[kind];
+    if (ms) *ms = ctx->prof_ms[kind];
+  });
+}
+
 int bem_destroy(bem_ctx* ctx) {
   if (!ctx) return BEM_OK;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  prof_collect(ctx);
+  for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return BEM_OK;

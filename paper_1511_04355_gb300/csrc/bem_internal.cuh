@@ -194,6 +194,13 @@ struct FreqSet {
   bool valid = false;
 };
 
+// Optional CUDA-event timing of kernel classes (enabled by bem_profile).
+enum ProfKind { PK_FAR32 = 0, PK_FAR64, PK_NEAR32, PK_NEAR64, PK_SELF, PK_VEC, PK_OTHER, PK_COUNT };
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+};
+
 }  // namespace bem
 
 struct bem_ctx {
@@ -211,6 +218,12 @@ struct bem_ctx {
   bem::DevBuf active;           // int32[F] per-frequency active flags
   int64_t launches = 0;         // kernels launched (accumulated, reset per call)
   int64_t f32_applies = 0, f64_applies = 0;
+  // kernel timing
+  bool prof = false;
+  std::vector<bem::ProfRec> prof_recs;
+  std::vector<cudaEvent_t> prof_pool;
+  double prof_ms[bem::PK_COUNT] = {0};
+  int64_t prof_n[bem::PK_COUNT] = {0};
 };
 
 namespace bem {
@@ -240,6 +253,16 @@ void known_data(bem_ctx* ctx, cx<double>* out);  // profile(s_f) * bc_value, [F]
 void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* st,
                  std::vector<int32_t>& iters, std::vector<int32_t>& refines,
                  std::vector<double>& resid, std::vector<int32_t>& status);
+
+// kernel timing: brackets the launches issued between begin and end with two events
+struct ProfScope {
+  bem_ctx* c;
+  int kind;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(bem_ctx* ctx, int k);
+  ~ProfScope();
+};
+void prof_collect(bem_ctx* ctx);  // synchronises and folds finished records into totals
 
 // helpers
 inline int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }

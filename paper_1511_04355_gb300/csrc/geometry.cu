@@ -564,6 +564,7 @@ void prepare_frequencies(bem_ctx* ctx, const double* s, int64_t F) {
   a.idx = nullptr;
   a.singular = sing.as<int>();
   const int64_t threads = 32 * F * me.ne;
+  ProfScope ps(ctx, PK_SELF);
   self_blocks_kernel<<<grid_for(threads, 128), 128, 0, ctx->stream>>>(a);
   BEM_LAUNCHED();
   ctx->launches++;

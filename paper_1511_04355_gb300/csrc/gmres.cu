@@ -320,6 +320,8 @@ int gmres_cycle(bem_ctx* ctx, Work& W, int64_t F, int64_t N, int m,
                                sizeof(cx<T>) * N, F, cudaMemcpyDeviceToDevice, st));
     Ops<T>::pre(ctx, w, z, act);
     Ops<T>::op(ctx, z, w, act);
+    {
+    ProfScope ps(ctx, PK_VEC);
     clear_hacc_kernel<<<grid_for(F * m1, 256), 256, 0, st>>>(s.hacc, F, m1, act);
     ctx->launches++;
     for (int pass = 0; pass < 2; ++pass) {
@@ -337,6 +339,7 @@ int gmres_cycle(bem_ctx* ctx, Work& W, int64_t F, int64_t N, int m,
     ctx->launches++;
     normalize_kernel<T><<<gv, 256, 0, st>>>(w, V, N, m1, j, act, s.inv_h);
     ctx->launches++;
+    }
     BEM_LAUNCHED();
     int32_t nact = 0;
     BEM_CUDA(cudaMemcpyAsync(&nact, s.nact, sizeof(int32_t), cudaMemcpyDeviceToHost, st));

@@ -366,6 +366,7 @@ static void launch_far(bem_ctx* ctx, const cx<R>* x, cx<R>* y, int which, const 
   BEM_CUDA(cudaFuncSetAttribute(far_kernel<R, TB, S, FT>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const dim3 grid(grid_for(a.ne, TB), grid_for(a.F, FT));
+  ProfScope ps(ctx, sizeof(R) == 4 ? PK_FAR32 : PK_FAR64);
   far_kernel<R, TB, S, FT><<<grid, TB, smem, ctx->stream>>>(a);
   BEM_LAUNCHED();
   ctx->launches++;
@@ -391,6 +392,7 @@ static void launch_near(bem_ctx* ctx, const cx<R>* x, cx<R>* y, int which, const
   a.ne = ctx->mesh.ne;
   a.F = ctx->fs.F;
   a.m = Geo<R>::m(ctx);
+  ProfScope ps(ctx, sizeof(R) == 4 ? PK_NEAR32 : PK_NEAR64);
   near_kernel<R><<<grid_for(a.F * a.ne, 128), 128, 0, ctx->stream>>>(a);
   BEM_LAUNCHED();
   ctx->launches++;
