@@ -142,6 +142,30 @@ int bem_set_bc(bem_ctx* ctx, const int8_t* bc_type, const double* bc_value, int 
 int bem_solve_frequencies(bem_ctx* ctx, const double* s, int64_t ns, double* x_out,
                           bem_solve_stats* stats);
 
+/* ------------------------------------------------------------------ time domain (FSM) */
+
+/* Fourier-series-method inverse Laplace transform (step a9; Sec. 2.2, Eqs. (invLap),
+ * (IDFT-MFT)), FP64:
+ *   out[j][d] = e^{eta t_j}/P [ W_0 Re h_0 + 2 Re sum_{k=1}^{nc-2} W_k h_k e^{i k w t_j}
+ *                               + W_{nc-1} Re(h_{nc-1} e^{i (nc-1) w t_j}) ],  w = 2 pi / P,
+ * from samples h[k][d] = h_d(eta + i k w), k = 0 .. nc-1 (N_s = 2 (nc - 1) points of the
+ * period P; the other half of the spectrum is the complex conjugate).  W_k = Hanning
+ * (1 + cos(2 pi k / N_s)) / 2 when window = 1, else 1.  The 1/P factor of the trapezoidal rule,
+ * absent from the printed equation, is included; any t is allowed (not only multiples of P/N_s).
+ * h: nc x m complex (interleaved), t: nt doubles, out: nt x m doubles; host or device.
+ * Errors: INVALID_ARG (nc < 2, m < 1, nt < 1, P <= 0, nc > 12800). */
+int bem_fsm_eval(bem_ctx* ctx, const double* h, int64_t nc, int64_t m, double eta, double period,
+                 const double* t, int64_t nt, int window, double* out);
+
+/* Frequency-domain approach with the FSM (Sec. 2.2): solves the BEM system at the nc
+ * frequencies s_k = eta + i k 2 pi / P (one batched bem_solve_frequencies) and returns the time
+ * responses of the requested unknowns at the times t (Hanning window).
+ * dofs: ndofs int64 indices into the 3 ne unknowns (host or device); resp_out: nt x ndofs
+ * doubles (host or device); stats: as for bem_solve_frequencies (arrays of length nc), nullable.
+ * A benchmark grid written s_k = sigma + i k pi / T is this grid with P = 2 T. */
+int bem_fsm(bem_ctx* ctx, double period, double eta, int64_t nc, const double* t, int64_t nt,
+            const int64_t* dofs, int64_t ndofs, double* resp_out, bem_solve_stats* stats);
+
 /* ------------------------------------------------------------------ operator-level calls
  * (the steps of one solve, exposed for verification and measurement) */
 

@@ -84,6 +84,9 @@ _SIGS = {
     "bem_rhs": (C.c_int, [_P, _P, _I64, _P]),
     "bem_precond_apply": (C.c_int, [_P, _P, _I64, _P, _P]),
     "bem_profile": (C.c_int, [_P, C.c_int]),
+    "bem_fsm_eval": (C.c_int, [_P, _P, _I64, _I64, C.c_double, C.c_double, _P, _I64, C.c_int, _P]),
+    "bem_fsm": (C.c_int, [_P, C.c_double, C.c_double, _I64, _P, _I64, _P, _I64, _P,
+                          C.POINTER(bem_solve_stats)]),
     "bem_kernel_time": (C.c_int, [_P, C.c_int, C.POINTER(_I64), C.POINTER(C.c_double)]),
 }
 
@@ -262,6 +265,44 @@ def bem_precond_apply(ctx, s, x, y=None):
     return y
 
 
+def bem_fsm_eval(ctx, h, eta, period, t, window=1, out=None):
+    """h: (nc, m) complex samples at eta + i k 2 pi / period; t: (nt,) -> (nt, m) response."""
+    h = np.ascontiguousarray(h, dtype=np.complex128) if isinstance(h, np.ndarray) else h
+    t = np.ascontiguousarray(t, dtype=np.float64) if isinstance(t, np.ndarray) else t
+    nc, m = h.shape
+    nt = t.shape[0]
+    if out is None:
+        out = np.zeros((nt, m), np.float64)
+    _check(ctx, load_library().bem_fsm_eval(ctx, _ptr(h), nc, m, eta, period, _ptr(t), nt, window,
+                                            _ptr(out)), "bem_fsm_eval")
+    return out
+
+
+def _stats_arrays(n):
+    stats = bem_solve_stats()
+    arr = dict(iterations=np.zeros(n, np.int32), refinements=np.zeros(n, np.int32),
+               residual=np.zeros(n, np.float64), status=np.zeros(n, np.int32))
+    stats.iterations = arr["iterations"].ctypes.data_as(C.POINTER(C.c_int32))
+    stats.refinements = arr["refinements"].ctypes.data_as(C.POINTER(C.c_int32))
+    stats.residual = arr["residual"].ctypes.data_as(C.POINTER(C.c_double))
+    stats.status = arr["status"].ctypes.data_as(C.POINTER(C.c_int32))
+    return stats, arr
+
+
+def bem_fsm(ctx, period, eta, nc, t, dofs, allow_not_converged=False):
+    """Solve at eta + i k 2 pi / period (k < nc) and return (nt, ndofs) time responses."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    d = np.ascontiguousarray(dofs, dtype=np.int64)
+    out = np.zeros((len(t), len(d)), np.float64)
+    stats, arr = _stats_arrays(nc)
+    rc = load_library().bem_fsm(ctx, period, eta, nc, _ptr(t), len(t), _ptr(d), len(d), _ptr(out),
+                                C.byref(stats))
+    if not (allow_not_converged and rc == BEM_ERR_NOT_CONVERGED):
+        _check(ctx, rc, "bem_fsm")
+    arr.update(kernel_launches=stats.kernel_launches, rc=rc)
+    return out, arr
+
+
 def bem_profile(ctx, enable=True):
     _check(ctx, load_library().bem_profile(ctx, 1 if enable else 0), "bem_profile")
 
@@ -329,6 +370,12 @@ class Context:
     def kernel_times(self):
         """{name: (launches, milliseconds)} since profile(True)."""
         return {name: bem_kernel_time(self.h, k) for k, name in KERNEL_NAMES.items()}
+
+    def fsm_eval(self, h, eta, period, t, window=1):
+        return bem_fsm_eval(self.h, h, eta, period, t, window)
+
+    def fsm(self, period, eta, nc, t, dofs, allow_not_converged=False):
+        return bem_fsm(self.h, period, eta, nc, t, dofs, allow_not_converged)
 
     def geometry(self):
         return bem_geometry(self.h, self.ne)

@@ -370,6 +370,80 @@ int bem_precond_apply(bem_ctx* ctx, const double* s, int64_t ns, const double* x
   });
 }
 
+int bem_fsm_eval(bem_ctx* ctx, const double* h, int64_t nc, int64_t m, double eta, double period,
+                 const double* t, int64_t nt, int window, double* out) {
+  return guarded(ctx, [&] {
+    BEM_REQUIRE(h && t && out, "null pointer");
+    fsm_check_args(nc, m, eta, period, nt, window);
+    ctx->io_c.reserve(sizeof(cx<double>) * nc * m);
+    ctx->io_d.reserve(sizeof(double) * nt);
+    ctx->io_e.reserve(sizeof(double) * nt * m);
+    ctx->fsm_table.reserve(sizeof(cx<double>) * nt * nc);
+    copy_in(ctx, ctx->io_c.p, h, sizeof(cx<double>) * nc * m);
+    copy_in(ctx, ctx->io_d.p, t, sizeof(double) * nt);
+    fsm_launch(ctx->io_c.as<cx<double>>(), nc, m, eta, period, ctx->io_d.as<double>(), nt, window,
+               ctx->io_e.as<double>(), ctx->fsm_table.as<cx<double>>(), ctx->stream);
+    ctx->launches += 2;
+    copy_out(ctx, out, ctx->io_e.p, sizeof(double) * nt * m);
+  });
+}
+
+int bem_fsm(bem_ctx* ctx, double period, double eta, int64_t nc, const double* t, int64_t nt,
+            const int64_t* dofs, int64_t ndofs, double* resp_out, bem_solve_stats* stats) {
+  int not_conv = 0;
+  const int rc = guarded(ctx, [&] {
+    need_mesh(ctx);
+    need_bc(ctx);
+    BEM_REQUIRE(t && dofs && resp_out, "null pointer");
+    fsm_check_args(nc, ndofs, eta, period, nt, 1);
+    BEM_REQUIRE(eta > 0, "eta must be > 0");
+    const int64_t N = 3 * ctx->mesh.ne;
+    std::vector<int64_t> hd(ndofs);
+    copy_out(ctx, hd.data(), dofs, sizeof(int64_t) * ndofs);
+    for (int64_t d = 0; d < ndofs; ++d) BEM_REQUIRE(hd[d] >= 0 && hd[d] < N, "dof index out of range");
+    std::vector<double> s(2 * nc);
+    for (int64_t k = 0; k < nc; ++k) {
+      s[2 * k] = eta;
+      s[2 * k + 1] = 2.0 * kPi * (double)k / period;
+    }
+    ctx->f32_applies = ctx->f64_applies = 0;
+    prepare_frequencies(ctx, s.data(), nc);
+    ctx->io_a.reserve(sizeof(cx<double>) * nc * N);
+    std::vector<int32_t> it, rf, status;
+    std::vector<double> res;
+    solve_batch(ctx, ctx->io_a.as<cx<double>>(), stats, it, rf, res, status);
+    for (int64_t f = 0; f < nc; ++f) not_conv |= (status[f] != 0);
+    DevBuf ddofs;
+    ddofs.reserve(sizeof(int64_t) * ndofs);
+    copy_in(ctx, ddofs.p, hd.data(), sizeof(int64_t) * ndofs);
+    ctx->io_c.reserve(sizeof(cx<double>) * nc * ndofs);
+    gather_dofs(ctx, ctx->io_a.as<cx<double>>(), N, nc, ddofs.as<int64_t>(), ndofs, ctx->io_c.as<cx<double>>());
+    ctx->io_d.reserve(sizeof(double) * nt);
+    ctx->io_e.reserve(sizeof(double) * nt * ndofs);
+    ctx->fsm_table.reserve(sizeof(cx<double>) * nt * nc);
+    copy_in(ctx, ctx->io_d.p, t, sizeof(double) * nt);
+    fsm_launch(ctx->io_c.as<cx<double>>(), nc, ndofs, eta, period, ctx->io_d.as<double>(), nt, 1,
+               ctx->io_e.as<double>(), ctx->fsm_table.as<cx<double>>(), ctx->stream);
+    ctx->launches += 2;
+    copy_out(ctx, resp_out, ctx->io_e.p, sizeof(double) * nt * ndofs);
+    if (stats) {
+      if (stats->iterations) std::memcpy(stats->iterations, it.data(), sizeof(int32_t) * nc);
+      if (stats->refinements) std::memcpy(stats->refinements, rf.data(), sizeof(int32_t) * nc);
+      if (stats->residual) std::memcpy(stats->residual, res.data(), sizeof(double) * nc);
+      if (stats->status) std::memcpy(stats->status, status.data(), sizeof(int32_t) * nc);
+      stats->fp32_operator_applies = ctx->f32_applies;
+      stats->fp64_operator_applies = ctx->f64_applies;
+      stats->kernel_launches = ctx->launches;
+    }
+  });
+  if (rc != BEM_OK) return rc;
+  if (not_conv) {
+    ctx->err = "some frequencies did not reach the tolerance (see stats.status)";
+    return BEM_ERR_NOT_CONVERGED;
+  }
+  return BEM_OK;
+}
+
 int bem_solve_frequencies(bem_ctx* ctx, const double* s, int64_t ns, double* x_out,
                           bem_solve_stats* stats) {
   int not_conv = 0;

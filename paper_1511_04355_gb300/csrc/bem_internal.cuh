@@ -215,6 +215,8 @@ struct bem_ctx {
   bem::FreqSet fs;
   // scratch buffers for vectors (grow-only)
   bem::DevBuf io_a, io_b;       // staging for ABI copies
+  bem::DevBuf io_c, io_d, io_e; // staging for the FSM calls (samples, times, output, dofs)
+  bem::DevBuf fsm_table;        // FSM phase table [nt][nc] complex
   bem::DevBuf active;           // int32[F] per-frequency active flags
   int64_t launches = 0;         // kernels launched (accumulated, reset per call)
   int64_t f32_applies = 0, f64_applies = 0;
@@ -263,6 +265,14 @@ struct ProfScope {
   ~ProfScope();
 };
 void prof_collect(bem_ctx* ctx);  // synchronises and folds finished records into totals
+
+// fsm.cu
+void fsm_check_args(int64_t nc, int64_t m, double eta, double period, int64_t nt, int window);
+void fsm_launch(const cx<double>* h, int64_t nc, int64_t m, double eta, double period,
+                const double* t, int64_t nt, int window, double* out, cx<double>* table,
+                cudaStream_t st);
+void gather_dofs(bem_ctx* ctx, const cx<double>* x, int64_t N, int64_t F, const int64_t* dofs_dev,
+                 int64_t nd, cx<double>* out);
 
 // helpers
 inline int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }
