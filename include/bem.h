@@ -166,6 +166,27 @@ int bem_fsm_eval(bem_ctx* ctx, const double* h, int64_t nc, int64_t m, double et
 int bem_fsm(bem_ctx* ctx, double period, double eta, int64_t nc, const double* t, int64_t nt,
             const int64_t* dofs, int64_t ndofs, double* resp_out, bem_solve_stats* stats);
 
+/* ------------------------------------------------------------------ allocation-free variant */
+
+/* bem_fsm_eval without any device allocation.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory while they run (a component confined
+ * to a fixed memory budget or to buffers handed to it by its host application, or a loop that
+ * must not stall on the device-wide synchronisation a cudaMalloc can cause) and therefore
+ * cannot create a bem_ctx.
+ * Same arithmetic and arguments as bem_fsm_eval, except: h, t and out must be device memory of
+ * the calling thread's current device; cuda_stream is the cudaStream_t to run on (NULL = the
+ * default stream); the call returns after the work completes.  Its only working memory is a
+ * fixed array of BEM_NOALLOC_FSM_TABLE complex doubles (4 MiB) that the library keeps on every
+ * device it is loaded on until the process exits, so nt * nc must not exceed
+ * BEM_NOALLOC_FSM_TABLE (INVALID_ARG with a message otherwise).  The first call on a device
+ * looks up that array's device address, so make it before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU race.  Errors: INVALID_ARG (sizes, host pointers,
+ * pointers of another device), CUDA; the message is returned by bem_noalloc_last_error(). */
+#define BEM_NOALLOC_FSM_TABLE 262144
+int bem_fsm_eval_noalloc(const double* h, int64_t nc, int64_t m, double eta, double period,
+                         const double* t, int64_t nt, int window, double* out, void* cuda_stream);
+const char* bem_noalloc_last_error(void);
+
 /* ------------------------------------------------------------------ operator-level calls
  * (the steps of one solve, exposed for verification and measurement) */
 

@@ -85,6 +85,9 @@ _SIGS = {
     "bem_precond_apply": (C.c_int, [_P, _P, _I64, _P, _P]),
     "bem_profile": (C.c_int, [_P, C.c_int]),
     "bem_fsm_eval": (C.c_int, [_P, _P, _I64, _I64, C.c_double, C.c_double, _P, _I64, C.c_int, _P]),
+    "bem_fsm_eval_noalloc": (C.c_int, [_P, _I64, _I64, C.c_double, C.c_double, _P, _I64, C.c_int,
+                                       _P, _P]),
+    "bem_noalloc_last_error": (C.c_char_p, []),
     "bem_fsm": (C.c_int, [_P, C.c_double, C.c_double, _I64, _P, _I64, _P, _I64, _P,
                           C.POINTER(bem_solve_stats)]),
     "bem_kernel_time": (C.c_int, [_P, C.c_int, C.POINTER(_I64), C.POINTER(C.c_double)]),
@@ -275,6 +278,19 @@ def bem_fsm_eval(ctx, h, eta, period, t, window=1, out=None):
         out = np.zeros((nt, m), np.float64)
     _check(ctx, load_library().bem_fsm_eval(ctx, _ptr(h), nc, m, eta, period, _ptr(t), nt, window,
                                             _ptr(out)), "bem_fsm_eval")
+    return out
+
+
+def bem_fsm_eval_noalloc(h, eta, period, t, out, window=1, stream=None):
+    """Allocation-free FSM inversion: h (nc, m) complex128, t (nt,), out (nt, m) float64 must be
+    CUDA tensors of the current device; stream: a cudaStream_t handle or None."""
+    nc, m = h.shape
+    nt = t.shape[0]
+    rc = load_library().bem_fsm_eval_noalloc(_ptr(h), nc, m, eta, period, _ptr(t), nt, window,
+                                             _ptr(out), stream)
+    if rc != BEM_OK:
+        msg = load_library().bem_noalloc_last_error()
+        raise BemError(rc, f"bem_fsm_eval_noalloc: {msg.decode() if msg else ''}")
     return out
 
 
