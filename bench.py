@@ -49,6 +49,7 @@ METRIC = "BEM frequency solves/s at 1e-6 rel. residual vs plain FP64 GPU; % FP32
 # kernel source (FMA = 2; exp/sin/cos on the special-function unit not counted)
 FLOPS_PER_UNIT_T = 159
 FLOPS_PER_UNIT_U = 113   # displacement-kernel (U) columns: the right-hand side pass
+FLOPS_PER_UNIT_RES = 221  # fused FP64 residual r = K k - A x: T and U per kernel evaluation
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP64_NOMINAL_TFLOPS = 1.25
 
@@ -325,30 +326,28 @@ def run_gpu(args):
 
     # roofline of the dominant kernel class (device time summed over the timed steps)
     clocks = clk.summary()
-    per_step = {k: (n / args.steps, ms / args.steps) for k, (n, ms) in ktimes.items()}
+    per_step = {k: (n / args.steps, ms / args.steps, fl / args.steps) for k, (n, ms, fl) in ktimes.items()}
     dominant = max(ktimes, key=lambda k: ktimes[k][1])
     info = infos[-1]
-    # FP32 far kernel units: every launch covers (ne^2 - ne) x 4 source points x active freqs;
-    # the number of frequency-launches is the iteration count summed over frequencies
-    f32_freq_launches = int(np.sum(info["iterations"]))
-    units32 = f32_freq_launches * (ne * ne - ne) * 4
-    n32, ms32 = per_step["far32"]
+    # FP32 far kernel units: every launch covers (ne^2 - ne) x 4 source points x its listed
+    # (active) frequencies; the library counts the frequency-launches
+    n32, ms32, fl32 = per_step["far32"]
+    units32 = fl32 * (ne * ne - ne) * 4
     peak32 = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     ach32 = units32 * FLOPS_PER_UNIT_T / (ms32 / 1e3) / 1e12 if ms32 > 0 else 0.0
-    # FP64 far kernel: the RHS pass (U columns, every frequency) + one T pass per refinement
-    flops64 = (N_FREQ * FLOPS_PER_UNIT_U + int(np.sum(info["refinements"])) * FLOPS_PER_UNIT_T) \
-        * (ne * ne - ne) * 4
-    n64, ms64 = per_step["far64"]
+    # FP64 refinement residual (fused U + T far-field sweep), one launch per refinement step
+    n64, ms64, fl64 = per_step["res64"]
+    flops64 = fl64 * (ne * ne - ne) * 4 * FLOPS_PER_UNIT_RES
     ach64 = flops64 / (ms64 / 1e3) / 1e12 if ms64 > 0 else 0.0
     roof32 = {"kernel": "far_kernel<float> (FP32 far-field operator)", "bound": "alu",
               "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
               "traffic": None, "launches_per_step": n32, "ms_per_step": ms32,
               "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (recipe unit counts, max clock)"}
-    roof64 = {"kernel": "far_kernel<double> (FP64 far-field operator: RHS and refinement residuals)",
+    roof64 = {"kernel": "far_kernel<double, resid> (FP64 refinement residual r = K k - A x)",
               "bound": "alu", "achieved": ach64, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
               "frac": ach64 / FP64_NOMINAL_TFLOPS, "traffic": None, "launches_per_step": n64,
               "ms_per_step": ms64, "peak_note": "nominal GB300 FP64 1.25 TFLOP/s (recipe table)"}
-    roofline = roof64 if dominant == "far64" else roof32
+    roofline = roof64 if dominant == "res64" else roof32
 
     cpu_v, cpu_sample, _ = (None, None, None)
     if ws == 1 and not args.skip_cpu:

@@ -53,12 +53,16 @@ extern "C" {
 
 #define BEM_PREC_FP64 0   /* plain FP64: FP64 operator, FP64 GMRES                            */
 #define BEM_PREC_MIXED 1  /* FP32 operator + FP32-stored Krylov basis with FP64 dot products,
-                             FP64 iterative refinement (residual and RHS in FP64)            */
+                             FP64 iterative refinement: every residual r = b - A x, with b
+                             formed from the boundary data in the same sweep, is FP64        */
 #define BEM_PREC_FP32 2   /* operator-only mode for bem_apply: FP32 far/near kernels          */
 
 #define BEM_APPLY_A 0     /* y = A(s) x : the system operator of Eq. (Aa_b)                  */
 #define BEM_APPLY_K 1     /* y = K(s) x : the operator acting on the known boundary data,
                              so that b(s) = K(s) (profile(s) * pattern)                       */
+
+#define BEM_RESID_DF64 0  /* far field of the residual in float-float (~2^-46) on the FP32 pipes */
+#define BEM_RESID_FP64 1  /* far field of the residual in native FP64                          */
 
 #define BEM_WARM_ZERO 0     /* GMRES starts from x0 = 0                                       */
 #define BEM_WARM_NEAREST 1  /* x0 = the stored solution at the nearest solved frequency      */
@@ -72,11 +76,14 @@ typedef struct bem_options {
   int32_t max_iters;   /* cap on GMRES iterations per inner solve (default 500)             */
   int32_t max_refine;  /* cap on FP64 refinement steps in MIXED mode (default 8)            */
   double tol;          /* target ||b - A x||_2 / ||b||_2, measured in FP64 (default 1e-6)   */
-  double inner_tol;    /* relative reduction asked of each FP32 inner solve (default 1e-5)  */
+  double inner_tol;    /* relative reduction asked of each FP32 inner solve (default 2e-7;
+                          never below 0.25 tol of the right-hand side)                     */
   int32_t warm_start;  /* BEM_WARM_* (default ZERO)                                          */
   int32_t freq_tile;   /* frequencies per operator tile, 0 = autotuned (default 0)          */
   int32_t use_graph;   /* capture GMRES iterations in CUDA graphs (default 1)                */
-  int32_t reserved[7];
+  int32_t residual_mode; /* MIXED refinement residual: BEM_RESID_DF64 (default) or
+                            BEM_RESID_FP64                                                    */
+  int32_t reserved[6];
 } bem_options;
 
 typedef struct bem_solve_stats {
@@ -217,6 +224,11 @@ int bem_apply(bem_ctx* ctx, const double* s, int64_t ns, const double* x, double
  * b_out: ns x 3ne complex doubles (host or device). */
 int bem_rhs(bem_ctx* ctx, const double* s, int64_t ns, double* b_out);
 
+/* Refinement residual (step a7): r_k = b(s_k) - A(s_k) x_k with b formed from the boundary
+ * data in the same sweep (r = K k - A x).  mode: BEM_RESID_DF64 or BEM_RESID_FP64 (far field
+ * arithmetic; near field and own element are FP64 in both).  x, r: ns x 3ne complex. */
+int bem_residual(bem_ctx* ctx, const double* s, int64_t ns, const double* x, double* r, int mode);
+
 /* Block-Jacobi preconditioner (step a5): y_k = D(s_k)^{-1} x_k with D the 3 x 3 diagonal
  * blocks A_ii(s_k) (free term + own-element integral).  FP64.  x, y: ns x 3ne complex. */
 int bem_precond_apply(bem_ctx* ctx, const double* s, int64_t ns, const double* x, double* y);
@@ -230,14 +242,17 @@ int bem_precond_apply(bem_ctx* ctx, const double* s, int64_t ns, const double* x
 #define BEM_KERNEL_NEAR64 3  /* FP64 near-field + own-element correction          */
 #define BEM_KERNEL_SELF 4    /* own-element singular blocks + preconditioner       */
 #define BEM_KERNEL_VEC 5     /* GMRES vector kernels of one Arnoldi step            */
+#define BEM_KERNEL_RES64 6   /* FP64 residual r = K k - A x (far field, fused U + T) */
 
 /* Enable (1) or disable (0) CUDA-event timing of the kernel classes above, on the context's
  * stream; resets the totals.  Timing adds two event records per timed launch. */
 int bem_profile(bem_ctx* ctx, int enable);
 
-/* Totals since bem_profile(ctx, 1): number of timed launches and summed device milliseconds
- * (events bracket each launch on the launching stream).  Errors: INVALID_ARG (bad kind). */
-int bem_kernel_time(bem_ctx* ctx, int kind, int64_t* launches, double* ms);
+/* Totals since bem_profile(ctx, 1): number of timed launches, summed device milliseconds
+ * (events bracket each launch on the launching stream) and, for the operator kernels, the
+ * number of frequencies the launches covered (each far/near launch computes the listed active
+ * frequencies only).  Any output pointer may be NULL.  Errors: INVALID_ARG (bad kind). */
+int bem_kernel_time(bem_ctx* ctx, int kind, int64_t* launches, double* ms, int64_t* freq_launches);
 
 #ifdef __cplusplus
 }

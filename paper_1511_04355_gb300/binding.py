@@ -33,6 +33,8 @@ BEM_PREC_MIXED = 1
 BEM_PREC_FP32 = 2
 BEM_APPLY_A = 0
 BEM_APPLY_K = 1
+BEM_RESID_DF64 = 0
+BEM_RESID_FP64 = 1
 BEM_WARM_ZERO = 0
 BEM_WARM_NEAREST = 1
 BEM_WARM_MLP = 2
@@ -42,7 +44,9 @@ BEM_KERNEL_NEAR32 = 2
 BEM_KERNEL_NEAR64 = 3
 BEM_KERNEL_SELF = 4
 BEM_KERNEL_VEC = 5
-KERNEL_NAMES = {0: "far32", 1: "far64", 2: "near32", 3: "near64", 4: "self", 5: "gmres_vec"}
+BEM_KERNEL_RES64 = 6
+KERNEL_NAMES = {0: "far32", 1: "far64", 2: "near32", 3: "near64", 4: "self", 5: "gmres_vec",
+                6: "res64"}
 
 
 class BemError(RuntimeError):
@@ -55,7 +59,7 @@ class bem_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("restart", C.c_int32), ("max_iters", C.c_int32),
                 ("max_refine", C.c_int32), ("tol", C.c_double), ("inner_tol", C.c_double),
                 ("warm_start", C.c_int32), ("freq_tile", C.c_int32), ("use_graph", C.c_int32),
-                ("reserved", C.c_int32 * 7)]
+                ("residual_mode", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class bem_solve_stats(C.Structure):
@@ -83,6 +87,7 @@ _SIGS = {
     "bem_apply": (C.c_int, [_P, _P, _I64, _P, _P, C.c_int, C.c_int]),
     "bem_rhs": (C.c_int, [_P, _P, _I64, _P]),
     "bem_precond_apply": (C.c_int, [_P, _P, _I64, _P, _P]),
+    "bem_residual": (C.c_int, [_P, _P, _I64, _P, _P, C.c_int]),
     "bem_profile": (C.c_int, [_P, C.c_int]),
     "bem_fsm_eval": (C.c_int, [_P, _P, _I64, _I64, C.c_double, C.c_double, _P, _I64, C.c_int, _P]),
     "bem_fsm_eval_noalloc": (C.c_int, [_P, _I64, _I64, C.c_double, C.c_double, _P, _I64, C.c_int,
@@ -90,7 +95,8 @@ _SIGS = {
     "bem_noalloc_last_error": (C.c_char_p, []),
     "bem_fsm": (C.c_int, [_P, C.c_double, C.c_double, _I64, _P, _I64, _P, _I64, _P,
                           C.POINTER(bem_solve_stats)]),
-    "bem_kernel_time": (C.c_int, [_P, C.c_int, C.POINTER(_I64), C.POINTER(C.c_double)]),
+    "bem_kernel_time": (C.c_int, [_P, C.c_int, C.POINTER(_I64), C.POINTER(C.c_double),
+                                  C.POINTER(_I64)]),
 }
 
 _lib = None
@@ -258,6 +264,17 @@ def bem_rhs(ctx, s, ne, b_out=None):
     return b_out
 
 
+def bem_residual(ctx, s, x, r=None, mode=BEM_RESID_DF64):
+    """r = b(s) - A(s) x (FP64-class refinement residual)."""
+    s, ns = _cplx_as_pairs(s)
+    if isinstance(x, np.ndarray):
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+        if r is None:
+            r = np.zeros_like(x)
+    _check(ctx, load_library().bem_residual(ctx, _ptr(s), ns, _ptr(x), _ptr(r), mode), "bem_residual")
+    return r
+
+
 def bem_precond_apply(ctx, s, x, y=None):
     s, ns = _cplx_as_pairs(s)
     x = np.ascontiguousarray(x, dtype=np.complex128) if isinstance(x, np.ndarray) else x
@@ -324,10 +341,13 @@ def bem_profile(ctx, enable=True):
 
 
 def bem_kernel_time(ctx, kind):
+    """(launches, milliseconds, frequency-launches) of a kernel class since bem_profile."""
     n = _I64()
     ms = C.c_double()
-    _check(ctx, load_library().bem_kernel_time(ctx, kind, C.byref(n), C.byref(ms)), "bem_kernel_time")
-    return n.value, ms.value
+    fl = _I64()
+    _check(ctx, load_library().bem_kernel_time(ctx, kind, C.byref(n), C.byref(ms), C.byref(fl)),
+           "bem_kernel_time")
+    return n.value, ms.value, fl.value
 
 
 class Context:
@@ -377,6 +397,9 @@ class Context:
     def rhs(self, s):
         return bem_rhs(self.h, s, self.ne)
 
+    def residual(self, s, x, mode=BEM_RESID_DF64):
+        return bem_residual(self.h, s, x, None, mode)
+
     def precond(self, s, x):
         return bem_precond_apply(self.h, s, x)
 
@@ -384,7 +407,7 @@ class Context:
         bem_profile(self.h, enable)
 
     def kernel_times(self):
-        """{name: (launches, milliseconds)} since profile(True)."""
+        """{name: (launches, milliseconds, frequency-launches)} since profile(True)."""
         return {name: bem_kernel_time(self.h, k) for k, name in KERNEL_NAMES.items()}
 
     def fsm_eval(self, h, eta, period, t, window=1):

@@ -41,7 +41,7 @@ static cudaEvent_t prof_event(bem_ctx* c) {
   return e;
 }
 
-ProfScope::ProfScope(bem_ctx* ctx, int k) : c(ctx), kind(k) {
+ProfScope::ProfScope(bem_ctx* ctx, int k, int64_t w) : c(ctx), kind(k), work(w) {
   if (!c->prof) return;
   a = prof_event(c);
   b = prof_event(c);
@@ -51,7 +51,7 @@ ProfScope::ProfScope(bem_ctx* ctx, int k) : c(ctx), kind(k) {
 ProfScope::~ProfScope() {
   if (!c->prof || !a) return;
   cudaEventRecord(b, c->stream);
-  c->prof_recs.push_back(ProfRec{kind, a, b});
+  c->prof_recs.push_back(ProfRec{kind, a, b, work});
 }
 
 void prof_collect(bem_ctx* c) {
@@ -61,6 +61,7 @@ void prof_collect(bem_ctx* c) {
     if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
       c->prof_ms[r.kind] += ms;
       c->prof_n[r.kind] += 1;
+      c->prof_work[r.kind] += r.work;
     }
     c->prof_pool.push_back(r.a);
     c->prof_pool.push_back(r.b);
@@ -75,6 +76,17 @@ __global__ void narrow_kernel(const cx<double>* a, cx<float>* b, int64_t n) {
 __global__ void widen_kernel(const cx<float>* a, cx<double>* b, int64_t n) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t < n) b[t] = mk((double)a[t].r, (double)a[t].i);
+}
+
+void narrow_array(bem_ctx* ctx, const cx<double>* a, cx<float>* b, int64_t n) {
+  narrow_kernel<<<grid_for(n, 256), 256, 0, ctx->stream>>>(a, b, n);
+  BEM_LAUNCHED();
+  ctx->launches++;
+}
+void widen_array(bem_ctx* ctx, const cx<float>* a, cx<double>* b, int64_t n) {
+  widen_kernel<<<grid_for(n, 256), 256, 0, ctx->stream>>>(a, b, n);
+  BEM_LAUNCHED();
+  ctx->launches++;
 }
 
 }  // namespace bem
@@ -122,10 +134,11 @@ int bem_default_options(bem_options* o) {
   o->max_iters = 500;
   o->max_refine = 8;
   o->tol = 1e-6;
-  o->inner_tol = 1e-5;
+  o->inner_tol = 2e-7;
   o->warm_start = BEM_WARM_ZERO;
   o->freq_tile = 0;
   o->use_graph = 1;
+  o->residual_mode = BEM_RESID_DF64;
   return BEM_OK;
 }
 
@@ -164,16 +177,18 @@ int bem_profile(bem_ctx* ctx, int enable) {
     for (int k = 0; k < PK_COUNT; ++k) {
       ctx->prof_ms[k] = 0;
       ctx->prof_n[k] = 0;
+      ctx->prof_work[k] = 0;
     }
   });
 }
 
-int bem_kernel_time(bem_ctx* ctx, int kind, int64_t* launches, double* ms) {
+int bem_kernel_time(bem_ctx* ctx, int kind, int64_t* launches, double* ms, int64_t* freq_launches) {
   return guarded(ctx, [&] {
     BEM_REQUIRE(kind >= 0 && kind < PK_COUNT, "unknown kernel class");
     prof_collect(ctx);
     if (launches) *launches = ctx->prof_n[kind];
     if (ms) *ms = ctx->prof_ms[kind];
+    if (freq_launches) *freq_launches = ctx->prof_work[kind];
   });
 }
 
@@ -206,6 +221,8 @@ int bem_set_options(bem_ctx* ctx, const bem_options* o) {
     BEM_REQUIRE(o->tol > 0 && o->tol < 1, "tol must be in (0, 1)");
     BEM_REQUIRE(o->inner_tol > 0 && o->inner_tol < 1, "inner_tol must be in (0, 1)");
     BEM_REQUIRE(o->warm_start >= BEM_WARM_ZERO && o->warm_start <= BEM_WARM_MLP, "bad warm_start");
+    BEM_REQUIRE(o->residual_mode == BEM_RESID_DF64 || o->residual_mode == BEM_RESID_FP64,
+                "residual_mode must be BEM_RESID_DF64 or BEM_RESID_FP64");
     ctx->opt = *o;
   });
 }
@@ -322,6 +339,7 @@ int bem_apply(bem_ctx* ctx, const double* s, int64_t ns, const double* x, double
     copy_in(ctx, ctx->io_a.p, x, sizeof(cx<double>) * n);
     if (precision == BEM_PREC_FP64) {
       apply_operator64(ctx, ctx->io_a.as<cx<double>>(), ctx->io_b.as<cx<double>>(), which, nullptr);
+      BEM_CUDA(cudaStreamSynchronize(ctx->stream));
     } else {
       DevBuf xf, yf;
       xf.reserve(sizeof(cx<float>) * n);
@@ -351,6 +369,25 @@ int bem_rhs(bem_ctx* ctx, const double* s, int64_t ns, double* b_out) {
     known_data(ctx, ctx->io_a.as<cx<double>>());
     apply_operator64(ctx, ctx->io_a.as<cx<double>>(), ctx->io_b.as<cx<double>>(), BEM_APPLY_K, nullptr);
     copy_out(ctx, b_out, ctx->io_b.p, sizeof(cx<double>) * n);
+  });
+}
+
+int bem_residual(bem_ctx* ctx, const double* s, int64_t ns, const double* x, double* r, int mode) {
+  return guarded(ctx, [&] {
+    need_mesh(ctx);
+    need_bc(ctx);
+    BEM_REQUIRE(s && x && r && ns >= 1, "bad argument");
+    BEM_REQUIRE(mode == BEM_RESID_DF64 || mode == BEM_RESID_FP64, "bad residual mode");
+    std::vector<double> sh(2 * ns);
+    copy_out(ctx, sh.data(), s, sizeof(double) * 2 * ns);
+    prepare_frequencies(ctx, sh.data(), ns);
+    const int64_t n = ns * 3 * ctx->mesh.ne;
+    ctx->io_a.reserve(sizeof(cx<double>) * n);
+    ctx->io_b.reserve(sizeof(cx<double>) * n);
+    copy_in(ctx, ctx->io_a.p, x, sizeof(cx<double>) * n);
+    if (mode == BEM_RESID_DF64) residual_df(ctx, ctx->io_a.as<cx<double>>(), ctx->io_b.as<cx<double>>(), nullptr);
+    else residual64(ctx, ctx->io_a.as<cx<double>>(), ctx->io_b.as<cx<double>>(), nullptr);
+    copy_out(ctx, r, ctx->io_b.p, sizeof(cx<double>) * n);
   });
 }
 

@@ -107,6 +107,9 @@ struct FreqC {
   cx<R> inv_a2;  // 1 / a^2
   R a_abs2;      // |a|^2
   R pad;
+  // phase slopes Im(s)/c_s and Im(s)/c_p as (hi, lo) pairs: the FP32 kernels form the phase
+  // omega r / c in float-float so that it carries ~1e-7 absolute error at |phase| ~ 60
+  R ai_hi, ai_lo, bi_hi, bi_lo;
 };
 
 // Four packed doubles (centroid + h, normal + area, quadrature point + weight).
@@ -163,6 +166,8 @@ struct Mesh {
   DevBuf c64, n64;             // D4[ne]:     (centroid, h), (normal, area)
   DevBuf q4_64, q7_64;         // double4-like [ne][4|7][4]
   DevBuf q4_32, q7_32;         // float4 [ne][4|7]
+  DevBuf q4_32lo, c32lo;       // float4: low parts (x - (float)x) of the 4-point rule points and
+                               // of the centroids, for float-float source-target distances
   DevBuf near_ptr, near_col;   // int32 CSR
   int64_t nnz = 0;
   std::vector<int32_t> h_near_ptr, h_near_col;
@@ -191,14 +196,16 @@ struct FreqSet {
   DevBuf Minv64;               // cx<double>[F][ne][9] inverse of A_ii
   DevBuf Minv32;               // cx<float>[F][ne][9]
   DevBuf pfac;                 // cx<double>[F] profile factor
+  DevBuf fcdf;                 // float-float frequency constants for the df64 residual
   bool valid = false;
 };
 
 // Optional CUDA-event timing of kernel classes (enabled by bem_profile).
-enum ProfKind { PK_FAR32 = 0, PK_FAR64, PK_NEAR32, PK_NEAR64, PK_SELF, PK_VEC, PK_OTHER, PK_COUNT };
+enum ProfKind { PK_FAR32 = 0, PK_FAR64, PK_NEAR32, PK_NEAR64, PK_SELF, PK_VEC, PK_RES64, PK_COUNT };
 struct ProfRec {
   int kind;
   cudaEvent_t a, b;
+  int64_t work;  // frequencies covered by the launch
 };
 
 }  // namespace bem
@@ -218,6 +225,9 @@ struct bem_ctx {
   bem::DevBuf io_c, io_d, io_e; // staging for the FSM calls (samples, times, output, dofs)
   bem::DevBuf fsm_table;        // FSM phase table [nt][nc] complex
   bem::DevBuf active;           // int32[F] per-frequency active flags
+  bem::DevBuf flist_d;          // int32 frequency list of the current operator launch
+  std::vector<int32_t> flist_h;
+  bem::DevBuf yacc;             // FP64 far-field accumulator [F][ne][3] complex
   int64_t launches = 0;         // kernels launched (accumulated, reset per call)
   int64_t f32_applies = 0, f64_applies = 0;
   // kernel timing
@@ -226,6 +236,7 @@ struct bem_ctx {
   std::vector<cudaEvent_t> prof_pool;
   double prof_ms[bem::PK_COUNT] = {0};
   int64_t prof_n[bem::PK_COUNT] = {0};
+  int64_t prof_work[bem::PK_COUNT] = {0};
 };
 
 namespace bem {
@@ -241,12 +252,21 @@ void element_blocks(bem_ctx* ctx, double sr, double si, const int32_t* rows,
                     const int32_t* cols, int64_t npairs, cx<double>* H, cx<double>* G);
 
 // operator.cu
-// y[f] = Op(s_f) x[f] for f with active[f] != 0 (active may be null = all).
+// y[f] = Op(s_f) x[f] for the frequencies in flist (null = all).
 // which = BEM_APPLY_A or BEM_APPLY_K.  x, y device pointers [F][ne][3] complex.
 void apply_operator64(bem_ctx* ctx, const cx<double>* x, cx<double>* y, int which,
-                      const int32_t* active);
+                      const std::vector<int32_t>* flist);
 void apply_operator32(bem_ctx* ctx, const cx<float>* x, cx<float>* y, int which,
-                      const int32_t* active);
+                      const std::vector<int32_t>* flist);
+// r[f] = K(s_f) k_f - A(s_f) x[f] in FP64 in one sweep (k = profile(s) * known data)
+void residual64(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::vector<int32_t>* flist);
+// the same with the far field in float-float arithmetic on the FP32 pipes (resid_df.cu)
+void residual_df(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::vector<int32_t>* flist);
+void build_freq_df(bem_ctx* ctx, const double* s, int64_t F);
+// helpers shared by the far kernels: stage the frequency list + zero the FP64 accumulator, and
+// the FP64 near-field/own-element pass of the residual
+int64_t stage_flist(bem_ctx* ctx, const std::vector<int32_t>* flist);
+void near_residual64(bem_ctx* ctx, const cx<double>* x, cx<double>* r, int64_t nfl);
 void apply_precond64(bem_ctx* ctx, const cx<double>* x, cx<double>* y, const int32_t* active);
 void apply_precond32(bem_ctx* ctx, const cx<float>* x, cx<float>* y, const int32_t* active);
 void known_data(bem_ctx* ctx, cx<double>* out);  // profile(s_f) * bc_value, [F][ne][3]
@@ -261,7 +281,8 @@ struct ProfScope {
   bem_ctx* c;
   int kind;
   cudaEvent_t a = nullptr, b = nullptr;
-  ProfScope(bem_ctx* ctx, int k);
+  int64_t work;
+  ProfScope(bem_ctx* ctx, int k, int64_t w = 0);
   ~ProfScope();
 };
 void prof_collect(bem_ctx* ctx);  // synchronises and folds finished records into totals
@@ -277,6 +298,8 @@ void gather_dofs(bem_ctx* ctx, const cx<double>* x, int64_t N, int64_t F, const 
 // helpers
 inline int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }
 bool is_device_ptr(const void* p);
+void narrow_array(bem_ctx* ctx, const cx<double>* a, cx<float>* b, int64_t n);
+void widen_array(bem_ctx* ctx, const cx<float>* a, cx<double>* b, int64_t n);
 void copy_in(bem_ctx* ctx, void* dst_dev, const void* src, size_t bytes);
 void copy_out(bem_ctx* ctx, void* dst, const void* src_dev, size_t bytes);
 

@@ -100,6 +100,7 @@ struct GeoArgs {
   D4 *c64, *n64;
   double *q4_64, *q7_64;
   float4 *q4_32, *q7_32;
+  float4 *q4_32lo, *c32lo;
   int* bad;  // set to 1 + element index of a degenerate triangle
 };
 
@@ -145,6 +146,8 @@ __global__ void geometry_kernel(GeoArgs a) {
     for (int c = 0; c < 3; ++c) a.tri64[9 * e + 3 * k + c] = p[k][c];
   a.c32[e] = make_float4((float)el.c[0], (float)el.c[1], (float)el.c[2], (float)el.h);
   a.c64[e] = D4{el.c[0], el.c[1], el.c[2], el.h};
+  a.c32lo[e] = make_float4((float)(el.c[0] - (double)(float)el.c[0]), (float)(el.c[1] - (double)(float)el.c[1]),
+                           (float)(el.c[2] - (double)(float)el.c[2]), 0.f);
   a.n64[e] = D4{el.n[0], el.n[1], el.n[2], el.area};
   a.n32[e] = make_float4((float)el.n[0], (float)el.n[1], (float)el.n[2], (float)el.area);
   for (int q = 0; q < 4; ++q) {
@@ -158,6 +161,8 @@ __global__ void geometry_kernel(GeoArgs a) {
     o[2] = y[2];
     o[3] = w;
     a.q4_32[4 * e + q] = make_float4((float)y[0], (float)y[1], (float)y[2], (float)w);
+    a.q4_32lo[4 * e + q] = make_float4((float)(y[0] - (double)(float)y[0]), (float)(y[1] - (double)(float)y[1]),
+                                       (float)(y[2] - (double)(float)y[2]), 0.f);
   }
   for (int q = 0; q < 7; ++q) {
     double y[3];
@@ -193,6 +198,8 @@ void build_geometry(bem_ctx* ctx) {
   m.q7_64.reserve(sizeof(double) * 28 * ne);
   m.q4_32.reserve(sizeof(float4) * 4 * ne);
   m.q7_32.reserve(sizeof(float4) * 7 * ne);
+  m.q4_32lo.reserve(sizeof(float4) * 4 * ne);
+  m.c32lo.reserve(sizeof(float4) * ne);
   GeoArgs a;
   a.verts = dv.as<double>();
   a.tris = dt.as<int32_t>();
@@ -213,6 +220,8 @@ void build_geometry(bem_ctx* ctx) {
   a.q7_64 = m.q7_64.as<double>();
   a.q4_32 = m.q4_32.as<float4>();
   a.q7_32 = m.q7_32.as<float4>();
+  a.q4_32lo = m.q4_32lo.as<float4>();
+  a.c32lo = m.c32lo.as<float4>();
   a.bad = dbad.as<int>();
   geometry_kernel<<<grid_for(ne, 128), 128, 0, ctx->stream>>>(a);
   BEM_LAUNCHED();
@@ -530,6 +539,15 @@ void prepare_frequencies(bem_ctx* ctx, const double* s, int64_t F) {
     h32[k].inv_a2 = mk((float)h64[k].inv_a2.r, (float)h64[k].inv_a2.i);
     h32[k].a_abs2 = (float)h64[k].a_abs2;
     h32[k].pad = 0;
+    const double bi = m.beta * a.i;
+    h32[k].ai_hi = (float)a.i;
+    h32[k].ai_lo = (float)(a.i - (double)h32[k].ai_hi);
+    h32[k].bi_hi = (float)bi;
+    h32[k].bi_lo = (float)(bi - (double)h32[k].bi_hi);
+    h64[k].ai_hi = a.i;
+    h64[k].ai_lo = 0;
+    h64[k].bi_hi = bi;
+    h64[k].bi_lo = 0;
     const double ss = sr * sr + si * si;
     pf[k] = (ctx->bc.profile == BEM_PROFILE_STEP) ? mk(sr / ss, -si / ss) : mk(1.0, 0.0);
   }
@@ -541,6 +559,7 @@ void prepare_frequencies(bem_ctx* ctx, const double* s, int64_t F) {
   BEM_CUDA(cudaMemcpyAsync(fs.fc64.p, h64.data(), sizeof(FreqC<double>) * F, cudaMemcpyHostToDevice, ctx->stream));
   BEM_CUDA(cudaMemcpyAsync(fs.fc32.p, h32.data(), sizeof(FreqC<float>) * F, cudaMemcpyHostToDevice, ctx->stream));
   BEM_CUDA(cudaMemcpyAsync(fs.pfac.p, pf.data(), sizeof(cx<double>) * F, cudaMemcpyHostToDevice, ctx->stream));
+  build_freq_df(ctx, s, F);
   const size_t nb = sizeof(cx<double>) * 9 * F * me.ne;
   fs.Tself.reserve(nb);
   fs.Gself.reserve(nb);
@@ -639,6 +658,10 @@ void element_blocks(bem_ctx* ctx, double sr, double si, const int32_t* rows, con
   fc.inv_a2 = mk(a2.r / n2, -a2.i / n2);
   fc.a_abs2 = fc.a.r * fc.a.r + fc.a.i * fc.a.i;
   fc.pad = 0;
+  fc.ai_hi = fc.a.i;
+  fc.ai_lo = 0;
+  fc.bi_hi = m.beta * fc.a.i;
+  fc.bi_lo = 0;
   for (int64_t k = 0; k < npairs; ++k)
     BEM_REQUIRE(rows[k] >= 0 && rows[k] < me.ne && cols[k] >= 0 && cols[k] < me.ne,
                 "element index out of range");

@@ -262,8 +262,8 @@ template <class T>
 struct Ops;
 template <>
 struct Ops<float> {
-  static void op(bem_ctx* c, const cx<float>* x, cx<float>* y, const int32_t* a) {
-    apply_operator32(c, x, y, BEM_APPLY_A, a);
+  static void op(bem_ctx* c, const cx<float>* x, cx<float>* y, const std::vector<int32_t>* l) {
+    apply_operator32(c, x, y, BEM_APPLY_A, l);
   }
   static void pre(bem_ctx* c, const cx<float>* x, cx<float>* y, const int32_t* a) {
     apply_precond32(c, x, y, a);
@@ -271,8 +271,8 @@ struct Ops<float> {
 };
 template <>
 struct Ops<double> {
-  static void op(bem_ctx* c, const cx<double>* x, cx<double>* y, const int32_t* a) {
-    apply_operator64(c, x, y, BEM_APPLY_A, a);
+  static void op(bem_ctx* c, const cx<double>* x, cx<double>* y, const std::vector<int32_t>* l) {
+    apply_operator64(c, x, y, BEM_APPLY_A, l);
   }
   static void pre(bem_ctx* c, const cx<double>* x, cx<double>* y, const int32_t* a) {
     apply_precond64(c, x, y, a);
@@ -283,7 +283,7 @@ struct Ops<double> {
 // from x = 0 of the correction; adds the correction to x64.  Returns iterations performed.
 template <class T>
 int gmres_cycle(bem_ctx* ctx, Work& W, int64_t F, int64_t N, int m,
-                std::vector<int32_t>& iters_host) {
+                std::vector<int32_t>& iters_host, const std::vector<int32_t>& part_h) {
   cudaStream_t st = ctx->stream;
   const int m1 = m + 1;
   GState s;
@@ -312,14 +312,16 @@ int gmres_cycle(bem_ctx* ctx, Work& W, int64_t F, int64_t N, int m,
       W.r.as<cx<double>>(), W.rn2.as<double>(), V, N, m1, act, s.g);
   BEM_LAUNCHED();
   ctx->launches++;
-  std::vector<int32_t> act_h(F);
+  std::vector<int32_t> act_h(F), list;
+  for (int64_t f = 0; f < F; ++f)
+    if (part_h[f]) list.push_back((int32_t)f);
   int it = 0;
   for (int j = 0; j < m; ++j) {
     // z = M^{-1} v_j: column j of V is strided by m1 N, gather it into w first
     BEM_CUDA(cudaMemcpy2DAsync(w, sizeof(cx<T>) * N, V + (size_t)j * N, sizeof(cx<T>) * N * m1,
                                sizeof(cx<T>) * N, F, cudaMemcpyDeviceToDevice, st));
     Ops<T>::pre(ctx, w, z, act);
-    Ops<T>::op(ctx, z, w, act);
+    Ops<T>::op(ctx, z, w, &list);
     {
     ProfScope ps(ctx, PK_VEC);
     clear_hacc_kernel<<<grid_for(F * m1, 256), 256, 0, st>>>(s.hacc, F, m1, act);
@@ -343,9 +345,13 @@ int gmres_cycle(bem_ctx* ctx, Work& W, int64_t F, int64_t N, int m,
     BEM_LAUNCHED();
     int32_t nact = 0;
     BEM_CUDA(cudaMemcpyAsync(&nact, s.nact, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    BEM_CUDA(cudaMemcpyAsync(act_h.data(), act, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, st));
     BEM_CUDA(cudaStreamSynchronize(st));
     ++it;
     if (nact == 0) break;
+    list.clear();
+    for (int64_t f = 0; f < F; ++f)
+      if (act_h[f]) list.push_back((int32_t)f);
   }
   // update: x += M^{-1} V y
   lsq_kernel<<<grid_for(F, 128), 128, 0, st>>>(s, F, m, part, W.y.as<cx<double>>());
@@ -401,14 +407,28 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
   W.nact.reserve(sizeof(int32_t));
   BEM_CUDA(cudaMemsetAsync(W.status.p, 0, sizeof(int32_t) * F, st));
 
-  // b = K (profile * data) in FP64
-  known_data(ctx, W.Ax.as<cx<double>>());
-  apply_operator64(ctx, W.Ax.as<cx<double>>(), W.b.as<cx<double>>(), BEM_APPLY_K, nullptr);
-  norm2_kernel<double><<<(unsigned)F, 256, 0, st>>>(W.b.as<cx<double>>(), N, nullptr, W.bn2.as<double>());
-  ctx->launches++;
+  if (mixed) {
+    // b in FP32 (K applied by the FP32 operator) seeds the first inner solve; the FP64 residual
+    // r = K k - A x of every refinement step recomputes the data term in FP64
+    known_data(ctx, W.Ax.as<cx<double>>());
+    DevBuf kf, bf;
+    kf.reserve(sizeof(cx<float>) * F * N);
+    bf.reserve(sizeof(cx<float>) * F * N);
+    narrow_array(ctx, W.Ax.as<cx<double>>(), kf.as<cx<float>>(), F * N);
+    apply_operator32(ctx, kf.as<cx<float>>(), bf.as<cx<float>>(), BEM_APPLY_K, nullptr);
+    widen_array(ctx, bf.as<cx<float>>(), W.r.as<cx<double>>(), F * N);
+    norm2_kernel<double><<<(unsigned)F, 256, 0, st>>>(W.r.as<cx<double>>(), N, nullptr, W.bn2.as<double>());
+    ctx->launches++;
+  } else {
+    // b = K (profile * data) in FP64
+    known_data(ctx, W.Ax.as<cx<double>>());
+    apply_operator64(ctx, W.Ax.as<cx<double>>(), W.b.as<cx<double>>(), BEM_APPLY_K, nullptr);
+    norm2_kernel<double><<<(unsigned)F, 256, 0, st>>>(W.b.as<cx<double>>(), N, nullptr, W.bn2.as<double>());
+    ctx->launches++;
+    BEM_CUDA(cudaMemcpyAsync(W.r.p, W.b.p, sizeof(cx<double>) * F * N, cudaMemcpyDeviceToDevice, st));
+  }
   // x = 0, r = b
   BEM_CUDA(cudaMemsetAsync(x_dev, 0, sizeof(cx<double>) * F * N, st));
-  BEM_CUDA(cudaMemcpyAsync(W.r.p, W.b.p, sizeof(cx<double>) * F * N, cudaMemcpyDeviceToDevice, st));
   BEM_CUDA(cudaMemcpyAsync(W.rn2.p, W.bn2.p, sizeof(double) * F, cudaMemcpyDeviceToDevice, st));
   std::vector<double> bn2(F), rn2(F), est(F), tgt(F);
   std::vector<int32_t> part(F, 1), stat(F);
@@ -441,7 +461,8 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
     if (total_inner >= o.max_iters) break;
     BEM_CUDA(cudaMemcpyAsync(W.part.p, part.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
     BEM_CUDA(cudaMemcpyAsync(W.target.p, tgt.data(), sizeof(double) * F, cudaMemcpyHostToDevice, st));
-    int it = mixed ? gmres_cycle<float>(ctx, W, F, N, m, iters) : gmres_cycle<double>(ctx, W, F, N, m, iters);
+    int it = mixed ? gmres_cycle<float>(ctx, W, F, N, m, iters, part)
+                   : gmres_cycle<double>(ctx, W, F, N, m, iters, part);
     total_inner += it;
     BEM_CUDA(cudaMemcpyAsync(est.data(), W.est.p, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
     BEM_CUDA(cudaMemcpyAsync(stat.data(), W.status.p, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, st));
@@ -473,15 +494,15 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
     }
     // FP64 residual r = b - A x for the instances still working
     BEM_CUDA(cudaMemcpyAsync(W.part.p, part.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
-    int64_t any = 0;
-    for (int64_t f = 0; f < F; ++f) any += part[f];
-    if (!any) break;
-    apply_operator64(ctx, x_dev, W.Ax.as<cx<double>>(), BEM_APPLY_A, W.part.as<int32_t>());
-    residual_kernel<<<grid_for(F * N, 256), 256, 0, st>>>(W.b.as<cx<double>>(), W.Ax.as<cx<double>>(),
-                                                          W.r.as<cx<double>>(), N, F, W.part.as<int32_t>());
+    std::vector<int32_t> rlist;
+    for (int64_t f = 0; f < F; ++f)
+      if (part[f]) rlist.push_back((int32_t)f);
+    if (rlist.empty()) break;
+    if (mixed && o.residual_mode == BEM_RESID_DF64) residual_df(ctx, x_dev, W.r.as<cx<double>>(), &rlist);
+    else residual64(ctx, x_dev, W.r.as<cx<double>>(), &rlist);
     norm2_kernel<double><<<(unsigned)F, 256, 0, st>>>(W.r.as<cx<double>>(), N, W.part.as<int32_t>(),
                                                       W.rn2.as<double>());
-    ctx->launches += 2;
+    ctx->launches += 1;
     BEM_LAUNCHED();
     BEM_CUDA(cudaMemcpyAsync(rn2.data(), W.rn2.p, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
     BEM_CUDA(cudaStreamSynchronize(st));

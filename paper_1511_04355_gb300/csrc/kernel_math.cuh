@@ -43,6 +43,19 @@ __device__ __forceinline__ cx<double> exp_neg(cx<double> z) {
   return mk(amp * cs, -amp * sn);
 }
 
+// e^{-(re + i ph)} for FP32 with the phase given as a float-float pair (ph_hi + ph_lo): the
+// Cody-Waite reduction acts on ph_hi and ph_lo is added after it, so the reduced argument keeps
+// ~1e-7 absolute accuracy even for |ph| ~ 100.
+__device__ __forceinline__ cx<float> exp_neg_ff(float re, float ph_hi, float ph_lo) {
+  const float amp = __expf(-re);
+  const float k = rintf(ph_hi * 0.159154943091895336f);
+  float red = fmaf(-k, 6.28318548202514648f, ph_hi);
+  red = fmaf(-k, -1.74845560007440834e-07f, red) + ph_lo;
+  float sn, cs;
+  __sincosf(red, &sn, &cs);
+  return mk(amp * cs, -amp * sn);
+}
+
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 
@@ -63,13 +76,32 @@ struct Radial {
   cx<R> Es, P, J, gs, gp;
 };
 
+// phase factors: FP64 uses z directly; FP32 rebuilds the phase omega r / c from the float-float
+// distance (r + r_lo) and float-float slopes
+__device__ __forceinline__ void phase_exps(cx<float> zs, cx<float> zp, float r, float r_lo,
+                                           const FreqC<float>& fc, cx<float>& Es, cx<float>& Ep) {
+  const float ps = fc.ai_hi * r;
+  const float ps_lo = fmaf(fc.ai_hi, r, -ps) + fmaf(fc.ai_hi, r_lo, fc.ai_lo * r);
+  const float pp = fc.bi_hi * r;
+  const float pp_lo = fmaf(fc.bi_hi, r, -pp) + fmaf(fc.bi_hi, r_lo, fc.bi_lo * r);
+  Es = exp_neg_ff(zs.r, ps, ps_lo);
+  Ep = exp_neg_ff(zp.r, pp, pp_lo);
+}
+__device__ __forceinline__ void phase_exps(cx<double> zs, cx<double> zp, double, double,
+                                           const FreqC<double>&, cx<double>& Es, cx<double>& Ep) {
+  Es = exp_neg(zs);
+  Ep = exp_neg(zp);
+}
+
+// r_lo: low part of the distance (float-float distance in the FP32 kernels, 0 otherwise)
 template <class R>
-__device__ __forceinline__ Radial<R> radial(R r, R inv_r2, const FreqC<R>& fc, const MatC<R>& m) {
+__device__ __forceinline__ Radial<R> radial(R r, R inv_r2, const FreqC<R>& fc, const MatC<R>& m,
+                                            R r_lo = R(0)) {
   Radial<R> o;
   const cx<R> zs = r * fc.a;
   const cx<R> zp = m.beta * zs;
-  o.Es = exp_neg(zs);
-  const cx<R> Ep = exp_neg(zp);
+  cx<R> Ep;
+  phase_exps(zs, zp, r, r_lo, fc, o.Es, Ep);
   o.gs = cfma(zs, o.Es, o.Es);
   o.gp = cfma(zp, Ep, Ep);
   o.P = axpy(-m.beta2, Ep, o.Es);

@@ -34,12 +34,18 @@ struct FarArgs {
   const typename V4<R>::T* q4;  // [ne][4] (x, y, z, w * area)
   const typename V4<R>::T* cen; // [ne] centroid (x, y, z, -)
   const typename V4<R>::T* nrm; // [ne] normal (x, y, z, -)
+  const float4* q4lo;           // FP32 only: low parts of q4 and of the centroids
+  const float4* cenlo;
   const int8_t* bc;             // [ne] or null (all traction-given)
-  int which;                    // BEM_APPLY_A / BEM_APPLY_K
+  int which;                    // BEM_APPLY_A / BEM_APPLY_K (apply mode)
   const cx<R>* x;               // [F][ne][3]
-  cx<R>* y;                     // [F][ne][3]
+  const double* bcv;            // [ne][3] known-data pattern (residual mode)
+  const cx<double>* pfac;       // [F] time-profile factor (residual mode)
+  double* yacc;                 // [F][ne][3] complex FP64 accumulator (atomic adds)
   const FreqC<R>* fc;           // [F]
-  const int32_t* active;        // [F] or null
+  const int32_t* flist;         // frequencies to compute (the active ones), nfl entries
+  int64_t nfl;
+  int64_t chunk;                // sources per split (multiple of the tile size)
   int64_t ne, F;
   MatC<R> m;
 };
@@ -52,45 +58,133 @@ __device__ __forceinline__ float column_code(const int8_t* bc, int64_t e, int wh
   return sign * (useU ? 2.f : 1.f);
 }
 
-template <class R, int TB, int S, int FT>
+// Source-target distance.  FP32: float-float difference of the float-float coordinates and a
+// float-float |d|^2, so that r carries ~1e-9 relative error (the phase omega r / c reaches ~60 rad
+// at the top of the band); rh, dr/dn and the weights only need single precision.  FP64: plain.
+template <class R>
+struct Dist {
+  R dx, dy, dz, r, r_lo, rinv;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ Dist<float> distance(float px, float py, float pz, float4 pl, float x0,
+                                                float x1, float x2, float4 xl, bool self) {
+  Dist<float> d;
+  float ex, ey, ez;
+  two_sum(px, -x0, d.dx, ex);
+  two_sum(py, -x1, d.dy, ey);
+  two_sum(pz, -x2, d.dz, ez);
+  const float lx = ex + (pl.x - xl.x), ly = ey + (pl.y - xl.y), lz = ez + (pl.z - xl.z);
+  const float sx = d.dx * d.dx, sy = d.dy * d.dy, sz = d.dz * d.dz;
+  const float qx = fmaf(d.dx, d.dx, -sx), qy = fmaf(d.dy, d.dy, -sy), qz = fmaf(d.dz, d.dz, -sz);
+  float s1, e1, s2, e2;
+  two_sum(sx, sy, s1, e1);
+  two_sum(s1, sz, s2, e2);
+  const float lo = (e1 + e2) + (qx + qy + qz) + 2.f * (d.dx * lx + d.dy * ly + d.dz * lz);
+  if (self) s2 = 1.f;
+  d.rinv = rsqrtf(s2);
+  d.r = s2 * d.rinv;
+  d.r_lo = self ? 0.f : (fmaf(-d.r, d.r, s2) + lo) * 0.5f * d.rinv;
+  return d;
+}
+
+__device__ __forceinline__ Dist<double> distance(double px, double py, double pz, float4, double x0,
+                                                 double x1, double x2, float4, bool self) {
+  Dist<double> d;
+  d.dx = px - x0;
+  d.dy = py - x1;
+  d.dz = pz - x2;
+  const double r2 = self ? 1.0 : d.dx * d.dx + d.dy * d.dy + d.dz * d.dz;
+  d.rinv = rsqrt(r2);
+  d.r = r2 * d.rinv;
+  d.r_lo = 0.0;
+  return d;
+}
+
+// T-kernel contribution of one source point to the three output components:
+//   o_c += cw [A (dr/dn v_c + (rh.v) n_c) + rh_c (q1 (n.v) + q2 dr/dn (rh.v))]
+template <class R>
+__device__ __forceinline__ void t_contract(const TCoef<R>& T, R cw, R drdn, R rh0, R rh1, R rh2,
+                                           R n0, R n1, R n2, cx<R> v0, cx<R> v1, cx<R> v2,
+                                           cx<R> nv, cx<R>* o) {
+  const cx<R> rv = mk(rh0 * v0.r + rh1 * v1.r + rh2 * v2.r, rh0 * v0.i + rh1 * v1.i + rh2 * v2.i);
+  const cx<R> t1 = (cw * drdn) * T.A;
+  const cx<R> t2 = (cw * T.A) * rv;
+  const cx<R> t3 = cw * cfma(T.q1, nv, drdn * (T.q2 * rv));
+  o[0] = cfma(t1, v0, axpy(n0, t2, axpy(rh0, t3, o[0])));
+  o[1] = cfma(t1, v1, axpy(n1, t2, axpy(rh1, t3, o[1])));
+  o[2] = cfma(t1, v2, axpy(n2, t2, axpy(rh2, t3, o[2])));
+}
+
+// U-kernel contribution: o_c += cu [(E_s - J) v_c - (P - 3J) rh_c (rh.v)]
+template <class R>
+__device__ __forceinline__ void u_contract(const Radial<R>& K, R cu, R rh0, R rh1, R rh2, cx<R> v0,
+                                           cx<R> v1, cx<R> v2, cx<R>* o) {
+  const cx<R> psi = cu * (K.Es - K.J);
+  const cx<R> rv = mk(rh0 * v0.r + rh1 * v1.r + rh2 * v2.r, rh0 * v0.i + rh1 * v1.i + rh2 * v2.i);
+  const cx<R> crv = (cu * axpy(R(-3), K.J, K.P)) * rv;
+  o[0] = cfma(psi, v0, axpy(-rh0, crv, o[0]));
+  o[1] = cfma(psi, v1, axpy(-rh1, crv, o[1]));
+  o[2] = cfma(psi, v2, axpy(-rh2, crv, o[2]));
+}
+
+// Far-field kernel.  Apply mode (RESID = false): y = Op x with Op = A or K, one kernel (T or U)
+// per source column.  Residual mode (RESID = true): y = K k - A x with k = profile(s) * known
+// data; every source contributes through both kernels, T applied to vT and U to vU where
+// (vT, vU) = (-x_e, k_e) for traction-given and (-k_e, x_e) for displacement-given columns.
+template <class R, int TB, int S, int FT, bool RESID>
 __global__ void __launch_bounds__(TB) far_kernel(const FarArgs<R> a) {
   using V = typename V4<R>::T;
+  constexpr int NV = RESID ? 7 : 4;                                    // cx per (source, freq)
+  constexpr bool FF = sizeof(R) == 4;                                  // float-float distances
+  constexpr int NL = FF ? 4 * S : 0;
   extern __shared__ __align__(32) unsigned char smem_raw[];
-  double* acc = reinterpret_cast<double*>(smem_raw);                 // [6 FT][TB]
-  V* sq = reinterpret_cast<V*>(acc + 6 * FT * TB);                    // [S][4]
+  // accumulators: per-tile partial sums (registers) are added into R-precision sums here, then
+  // into the FP64 result with one atomic add per output at the end
+  R* acc = reinterpret_cast<R*>(smem_raw);                            // [6 FT][TB]
+  V* sq = reinterpret_cast<V*>(smem_raw + sizeof(R) * 6 * FT * TB);   // [S][4]
   V* sn = sq + 4 * S;                                                  // [S]
-  cx<R>* sv = reinterpret_cast<cx<R>*>(sn + S);                       // [S][FT][4]
-  FreqC<R>* sfc = reinterpret_cast<FreqC<R>*>(sv + 4 * FT * S);       // [FT]
+  float4* sql = reinterpret_cast<float4*>(sn + S);                    // [S][4] low parts (FP32)
+  cx<R>* sv = reinterpret_cast<cx<R>*>(sql + NL);                     // [S][FT][NV]
+  FreqC<R>* sfc = reinterpret_cast<FreqC<R>*>(sv + NV * FT * S);      // [FT]
 
   const int tid = threadIdx.x;
-  const int64_t f0 = (int64_t)blockIdx.y * FT;
-  const int nf = (int)min((int64_t)FT, a.F - f0);
-  unsigned mask = 0;
-  for (int k = 0; k < nf; ++k)
-    if (!a.active || a.active[f0 + k]) mask |= 1u << k;
-  if (mask == 0) return;
+  const int64_t g0 = (int64_t)blockIdx.y * FT;   // position in the frequency list
+  const int nf = (int)min((int64_t)FT, a.nfl - g0);
+  const unsigned mask = (1u << nf) - 1u;
+  const int64_t src0 = (int64_t)blockIdx.z * a.chunk;
+  const int64_t src1 = min(a.ne, src0 + a.chunk);
   const int64_t i = (int64_t)blockIdx.x * TB + tid;
   const bool valid = i < a.ne;
   R xi0 = 0, xi1 = 0, xi2 = 0;
+  float4 xil = make_float4(0.f, 0.f, 0.f, 0.f);
   if (valid) {
     const V c = a.cen[i];
     xi0 = c.x;
     xi1 = c.y;
     xi2 = c.z;
+    if (FF) xil = a.cenlo[i];
   }
   if (tid < FT) {
-    if (tid < nf) sfc[tid] = a.fc[f0 + tid];
+    if (tid < nf) sfc[tid] = a.fc[a.flist[g0 + tid]];
     else sfc[tid] = FreqC<R>{};
   }
 #pragma unroll
-  for (int k = 0; k < 6 * FT; ++k) acc[k * TB + tid] = 0.0;
+  for (int k = 0; k < 6 * FT; ++k) acc[k * TB + tid] = R(0);
   const MatC<R>& m = a.m;
   const R inv4pi = R(kInv4Pi);
 
-  for (int64_t e0 = 0; e0 < a.ne; e0 += S) {
-    const int ns = (int)min((int64_t)S, a.ne - e0);
+  for (int64_t e0 = src0; e0 < src1; e0 += S) {
+    const int ns = (int)min((int64_t)S, src1 - e0);
     __syncthreads();
     for (int t = tid; t < 4 * ns; t += TB) sq[t] = a.q4[4 * e0 + t];
+    if (FF)
+      for (int t = tid; t < 4 * ns; t += TB) sql[t] = a.q4lo[4 * e0 + t];
     for (int t = tid; t < ns; t += TB) {
       V n = a.nrm[e0 + t];
       n.w = (R)column_code(a.bc, e0 + t, a.which);
@@ -98,19 +192,41 @@ __global__ void __launch_bounds__(TB) far_kernel(const FarArgs<R> a) {
     }
     for (int t = tid; t < ns * FT; t += TB) {
       const int e = t / FT, k = t % FT;
-      cx<R> v0 = mk(R(0), R(0)), v1 = v0, v2 = v0;
+      const int64_t ge = e0 + e;
+      cx<R> v0 = mk(R(0), R(0)), v1 = v0, v2 = v0, k0 = v0, k1 = v0, k2 = v0;
       if (k < nf) {
-        const cx<R>* xv = a.x + ((f0 + k) * a.ne + e0 + e) * 3;
+        const int64_t f = a.flist[g0 + k];
+        const cx<R>* xv = a.x + (f * a.ne + ge) * 3;
         v0 = xv[0];
         v1 = xv[1];
         v2 = xv[2];
+        if (RESID) {
+          const cx<double> pf = a.pfac[f];
+          const double* kv = a.bcv + 3 * ge;
+          k0 = mk((R)(pf.r * kv[0]), (R)(pf.i * kv[0]));
+          k1 = mk((R)(pf.r * kv[1]), (R)(pf.i * kv[1]));
+          k2 = mk((R)(pf.r * kv[2]), (R)(pf.i * kv[2]));
+        }
       }
-      const V n = a.nrm[e0 + e];
-      cx<R>* o = sv + 4 * (e * FT + k);
-      o[0] = v0;
-      o[1] = v1;
-      o[2] = v2;
-      o[3] = mk(n.x * v0.r + n.y * v1.r + n.z * v2.r, n.x * v0.i + n.y * v1.i + n.z * v2.i);
+      const V n = a.nrm[ge];
+      cx<R>* o = sv + NV * (e * FT + k);
+      if (RESID) {
+        const bool dir = a.bc && a.bc[ge] == BEM_BC_DISPLACEMENT;
+        const cx<R> t0 = dir ? k0 : v0, t1 = dir ? k1 : v1, t2 = dir ? k2 : v2;
+        const cx<R> u0 = dir ? v0 : k0, u1 = dir ? v1 : k1, u2 = dir ? v2 : k2;
+        o[0] = R(-1) * t0;
+        o[1] = R(-1) * t1;
+        o[2] = R(-1) * t2;
+        o[3] = mk(-(n.x * t0.r + n.y * t1.r + n.z * t2.r), -(n.x * t0.i + n.y * t1.i + n.z * t2.i));
+        o[4] = u0;
+        o[5] = u1;
+        o[6] = u2;
+      } else {
+        o[0] = v0;
+        o[1] = v1;
+        o[2] = v2;
+        o[3] = mk(n.x * v0.r + n.y * v1.r + n.z * v2.r, n.x * v0.i + n.y * v1.i + n.z * v2.i);
+      }
     }
     __syncthreads();
 
@@ -122,52 +238,36 @@ __global__ void __launch_bounds__(TB) far_kernel(const FarArgs<R> a) {
       const V nn = sn[e];
       const bool self = (e0 + e == i);
       const bool isU = fabs((float)nn.w) > 1.5f;
-      const R sign = nn.w > 0 ? R(1) : R(-1);
-#pragma unroll
+      const R sign = RESID ? R(1) : (nn.w > 0 ? R(1) : R(-1));
+#pragma unroll 1
       for (int q = 0; q < 4; ++q) {
         const V p = sq[4 * e + q];
-        const R dx = p.x - xi0, dy = p.y - xi1, dz = p.z - xi2;
-        const R r2 = self ? R(1) : dx * dx + dy * dy + dz * dz;
-        const R rinv = rsqrt_r(r2);
-        const R r = r2 * rinv;
+        const Dist<R> D = distance(p.x, p.y, p.z, FF ? sql[4 * e + q] : make_float4(0.f, 0.f, 0.f, 0.f),
+                                   xi0, xi1, xi2, xil, self);
+        const R r = D.r, rinv = D.rinv, r_lo = D.r_lo;
         const R inv_r2 = rinv * rinv;
-        const R rh0 = dx * rinv, rh1 = dy * rinv, rh2 = dz * rinv;
+        const R rh0 = D.dx * rinv, rh1 = D.dy * rinv, rh2 = D.dz * rinv;
         const R w = self ? R(0) : p.w * sign;
-        if (!isU) {
-          const R drdn = rh0 * nn.x + rh1 * nn.y + rh2 * nn.z;
-          const R cw = w * inv_r2 * inv4pi;
-          const R cwd = cw * drdn;
+        const R drdn = rh0 * nn.x + rh1 * nn.y + rh2 * nn.z;
+        const R cw = w * inv_r2 * inv4pi;
+        const R cu = w * rinv * m.inv4pimu;
+        if (RESID || !isU) {
 #pragma unroll
           for (int k = 0; k < FT; ++k) {
             if (!((mask >> k) & 1u)) continue;
-            const FreqC<R> fc = sfc[k];
-            const cx<R>* v = sv + 4 * (e * FT + k);
-            const cx<R> v0 = v[0], v1 = v[1], v2 = v[2], nv = v[3];
-            const Radial<R> K = radial(r, inv_r2, fc, m);
+            const cx<R>* v = sv + NV * (e * FT + k);
+            const Radial<R> K = radial(r, inv_r2, sfc[k], m, r_lo);
             const TCoef<R> T = tcoef(K, m);
-            const cx<R> rv = mk(rh0 * v0.r + rh1 * v1.r + rh2 * v2.r, rh0 * v0.i + rh1 * v1.i + rh2 * v2.i);
-            const cx<R> t1 = cwd * T.A;
-            const cx<R> t2 = (cw * T.A) * rv;
-            const cx<R> t3 = cw * cfma(T.q1, nv, drdn * (T.q2 * rv));
-            part[k][0] = cfma(t1, v0, axpy(nn.x, t2, axpy(rh0, t3, part[k][0])));
-            part[k][1] = cfma(t1, v1, axpy(nn.y, t2, axpy(rh1, t3, part[k][1])));
-            part[k][2] = cfma(t1, v2, axpy(nn.z, t2, axpy(rh2, t3, part[k][2])));
+            t_contract(T, cw, drdn, rh0, rh1, rh2, nn.x, nn.y, nn.z, v[0], v[1], v[2], v[3], part[k]);
+            if (RESID) u_contract(K, cu, rh0, rh1, rh2, v[4], v[5], v[6], part[k]);
           }
         } else {
-          const R cu = w * rinv * m.inv4pimu;
 #pragma unroll
           for (int k = 0; k < FT; ++k) {
             if (!((mask >> k) & 1u)) continue;
-            const FreqC<R> fc = sfc[k];
-            const cx<R>* v = sv + 4 * (e * FT + k);
-            const cx<R> v0 = v[0], v1 = v[1], v2 = v[2];
-            const Radial<R> K = radial(r, inv_r2, fc, m);
-            const cx<R> psi = cu * (K.Es - K.J);
-            const cx<R> rv = mk(rh0 * v0.r + rh1 * v1.r + rh2 * v2.r, rh0 * v0.i + rh1 * v1.i + rh2 * v2.i);
-            const cx<R> crv = (cu * axpy(R(-3), K.J, K.P)) * rv;
-            part[k][0] = cfma(psi, v0, axpy(-rh0, crv, part[k][0]));
-            part[k][1] = cfma(psi, v1, axpy(-rh1, crv, part[k][1]));
-            part[k][2] = cfma(psi, v2, axpy(-rh2, crv, part[k][2]));
+            const cx<R>* v = sv + NV * (e * FT + k);
+            const Radial<R> K = radial(r, inv_r2, sfc[k], m, r_lo);
+            u_contract(K, cu, rh0, rh1, rh2, v[0], v[1], v[2], part[k]);
           }
         }
       }
@@ -176,26 +276,25 @@ __global__ void __launch_bounds__(TB) far_kernel(const FarArgs<R> a) {
     for (int k = 0; k < FT; ++k)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        acc[(6 * k + 2 * c) * TB + tid] += (double)part[k][c].r;
-        acc[(6 * k + 2 * c + 1) * TB + tid] += (double)part[k][c].i;
+        acc[(6 * k + 2 * c) * TB + tid] += part[k][c].r;
+        acc[(6 * k + 2 * c + 1) * TB + tid] += part[k][c].i;
       }
   }
   if (!valid) return;
 #pragma unroll
   for (int k = 0; k < FT; ++k) {
     if (!((mask >> k) & 1u)) continue;
-    cx<R>* yo = a.y + ((f0 + k) * a.ne + i) * 3;
+    double* yo = a.yacc + ((int64_t)a.flist[g0 + k] * a.ne + i) * 6;
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-      yo[c] = mk((R)acc[(6 * k + 2 * c) * TB + tid], (R)acc[(6 * k + 2 * c + 1) * TB + tid]);
+    for (int c = 0; c < 6; ++c) atomicAdd(yo + c, (double)acc[(6 * k + c) * TB + tid]);
   }
 }
 
-template <class R, int TB, int S, int FT>
+template <class R, int TB, int S, int FT, bool RESID>
 static size_t far_smem() {
   using V = typename V4<R>::T;
-  return sizeof(double) * 6 * FT * TB + sizeof(V) * 5 * S + sizeof(cx<R>) * 4 * FT * S +
-         sizeof(FreqC<R>) * FT;
+  return sizeof(R) * 6 * FT * TB + sizeof(V) * 5 * S + (sizeof(R) == 4 ? sizeof(float4) * 4 * S : 0) +
+         sizeof(cx<R>) * (RESID ? 7 : 4) * FT * S + sizeof(FreqC<R>) * FT;
 }
 
 // ------------------------------------------------------------------------------- near field
@@ -208,86 +307,113 @@ struct NearArgs {
   const int32_t *ptr, *col;
   const int8_t* bc;
   int which;
+  bool resid;               // residual mode: y = K k - A x
+  const double* bcv;        // [ne][3] known-data pattern (residual mode)
+  const cx<double>* pfac;   // [F]
   const cx<double>* Tself;  // [F][ne][9]
   const cx<double>* Gself;
   const cx<R>* x;
   cx<R>* y;
+  const double* yacc;       // far-field sums [F][ne][3] complex
   const FreqC<R>* fc;
-  const int32_t* active;
+  const int32_t* flist;
+  int64_t nfl;
   int64_t ne, F;
   MatC<R> m;
 };
 
+// one source point: T contraction with vT (if useT) and U contraction with vU (if useU)
 template <class R>
 __device__ __forceinline__ void add_point(R xi0, R xi1, R xi2, const typename V4<R>::T& p, R wsign,
-                                          const typename V4<R>::T& nn, bool isU,
-                                          const FreqC<R>& fc, const MatC<R>& m, const cx<R>* v,
-                                          cx<R> nv, cx<R>* o) {
+                                          const typename V4<R>::T& nn, bool useT, bool useU,
+                                          const FreqC<R>& fc, const MatC<R>& m, const cx<R>* vT,
+                                          cx<R> nvT, const cx<R>* vU, cx<R>* o) {
   const R dx = p.x - xi0, dy = p.y - xi1, dz = p.z - xi2;
   const R r2 = dx * dx + dy * dy + dz * dz;
   const R rinv = rsqrt_r(r2), r = r2 * rinv, inv_r2 = rinv * rinv;
-  const R rh[3] = {dx * rinv, dy * rinv, dz * rinv};
+  const R rh0 = dx * rinv, rh1 = dy * rinv, rh2 = dz * rinv;
   const Radial<R> K = radial(r, inv_r2, fc, m);
-  const cx<R> rv = mk(rh[0] * v[0].r + rh[1] * v[1].r + rh[2] * v[2].r,
-                      rh[0] * v[0].i + rh[1] * v[1].i + rh[2] * v[2].i);
-  if (!isU) {
-    const R drdn = rh[0] * nn.x + rh[1] * nn.y + rh[2] * nn.z;
+  if (useT) {
+    const R drdn = rh0 * nn.x + rh1 * nn.y + rh2 * nn.z;
     const R cw = p.w * wsign * inv_r2 * R(kInv4Pi);
-    const TCoef<R> T = tcoef(K, m);
-    const cx<R> t1 = (cw * drdn) * T.A;
-    const cx<R> t2 = (cw * T.A) * rv;
-    const cx<R> t3 = cw * cfma(T.q1, nv, drdn * (T.q2 * rv));
-    const R nvec[3] = {nn.x, nn.y, nn.z};
-    for (int c = 0; c < 3; ++c) o[c] = cfma(t1, v[c], axpy(nvec[c], t2, axpy(rh[c], t3, o[c])));
-  } else {
-    const R cu = p.w * wsign * rinv * m.inv4pimu;
-    const cx<R> psi = cu * (K.Es - K.J);
-    const cx<R> crv = (cu * axpy(R(-3), K.J, K.P)) * rv;
-    for (int c = 0; c < 3; ++c) o[c] = cfma(psi, v[c], axpy(-rh[c], crv, o[c]));
+    t_contract(tcoef(K, m), cw, drdn, rh0, rh1, rh2, nn.x, nn.y, nn.z, vT[0], vT[1], vT[2], nvT, o);
   }
+  if (useU) u_contract(K, p.w * wsign * rinv * m.inv4pimu, rh0, rh1, rh2, vU[0], vU[1], vU[2], o);
 }
 
 template <class R>
 __global__ void near_kernel(const NearArgs<R> a) {
   using V = typename V4<R>::T;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= a.F * a.ne) return;
-  const int64_t f = t / a.ne, i = t % a.ne;
-  if (a.active && !a.active[f]) return;
+  if (t >= a.nfl * a.ne) return;
+  const int64_t f = a.flist[t / a.ne], i = t % a.ne;
   const V c = a.cen[i];
   const FreqC<R> fc = a.fc[f];
+  const cx<double> pf = a.resid ? a.pfac[f] : mk(0.0, 0.0);
   cx<R> o[3] = {mk(R(0), R(0)), mk(R(0), R(0)), mk(R(0), R(0))};
-  for (int32_t p = a.ptr[i]; p < a.ptr[i + 1]; ++p) {
-    const int64_t e = a.col[p];
-    const float code = column_code(a.bc, e, a.which);
-    const bool isU = fabsf(code) > 1.5f;
-    const R sign = code > 0 ? R(1) : R(-1);
+  // source vectors of element e: apply mode -> (v, v) with the column's kernel; residual mode
+  // -> vT = -x or -k, vU = k or x (see far_kernel)
+  auto load = [&](int64_t e, cx<R>* vT, cx<R>& nvT, cx<R>* vU, bool& useT, bool& useU, R& sign) {
     const V nn = a.nrm[e];
     const cx<R>* xv = a.x + (f * a.ne + e) * 3;
-    const cx<R> v[3] = {xv[0], xv[1], xv[2]};
-    const cx<R> nv = mk(nn.x * v[0].r + nn.y * v[1].r + nn.z * v[2].r,
-                        nn.x * v[0].i + nn.y * v[1].i + nn.z * v[2].i);
-    for (int q = 0; q < 7; ++q) add_point(c.x, c.y, c.z, a.q7[7 * e + q], sign, nn, isU, fc, a.m, v, nv, o);
-    for (int q = 0; q < 4; ++q) add_point(c.x, c.y, c.z, a.q4[4 * e + q], -sign, nn, isU, fc, a.m, v, nv, o);
-  }
-  // own element: A_ii or K_ii from the FP64 singular blocks
-  const int b = a.bc ? (int)a.bc[i] : 0;
-  const bool useU = (b ^ a.which) != 0;
-  const double sg = b ? -1.0 : 1.0;
-  const cx<double>* blk = (useU ? a.Gself : a.Tself) + (f * a.ne + i) * 9;
-  const cx<R>* xv = a.x + (f * a.ne + i) * 3;
-  const cx<R> v[3] = {xv[0], xv[1], xv[2]};
-  for (int r = 0; r < 3; ++r) {
-    cx<R> s = mk(R(0), R(0));
-    for (int cc = 0; cc < 3; ++cc) {
-      cx<double> d = blk[3 * r + cc];
-      if (!useU && r == cc) d.r += 0.5;
-      s = cfma(mk((R)(sg * d.r), (R)(sg * d.i)), v[cc], s);
+    if (!a.resid) {
+      const float code = column_code(a.bc, e, a.which);
+      useU = fabsf(code) > 1.5f;
+      useT = !useU;
+      sign = code > 0 ? R(1) : R(-1);
+      for (int q = 0; q < 3; ++q) vT[q] = vU[q] = xv[q];
+    } else {
+      useT = useU = true;
+      sign = R(1);
+      const bool dir = a.bc && a.bc[e] == BEM_BC_DISPLACEMENT;
+      for (int q = 0; q < 3; ++q) {
+        const double kv = a.bcv[3 * e + q];
+        const cx<R> kq = mk((R)(pf.r * kv), (R)(pf.i * kv));
+        vT[q] = R(-1) * (dir ? kq : xv[q]);
+        vU[q] = dir ? xv[q] : kq;
+      }
     }
-    o[r] = o[r] + s;
+    nvT = mk(nn.x * vT[0].r + nn.y * vT[1].r + nn.z * vT[2].r, nn.x * vT[0].i + nn.y * vT[1].i + nn.z * vT[2].i);
+  };
+  for (int32_t p = a.ptr[i]; p < a.ptr[i + 1]; ++p) {
+    const int64_t e = a.col[p];
+    cx<R> vT[3], vU[3], nvT;
+    bool useT, useU;
+    R sign;
+    load(e, vT, nvT, vU, useT, useU, sign);
+    const V nn = a.nrm[e];
+    for (int q = 0; q < 7; ++q)
+      add_point(c.x, c.y, c.z, a.q7[7 * e + q], sign, nn, useT, useU, fc, a.m, vT, nvT, vU, o);
+    for (int q = 0; q < 4; ++q)
+      add_point(c.x, c.y, c.z, a.q4[4 * e + q], -sign, nn, useT, useU, fc, a.m, vT, nvT, vU, o);
+  }
+  // own element from the FP64 singular blocks: H_ii' = 1/2 I + H_ii applied to vT, G_ii to vU
+  {
+    cx<R> vT[3], vU[3], nvT;
+    bool useT, useU;
+    R sign;
+    load(i, vT, nvT, vU, useT, useU, sign);
+    const cx<double>* Hb = a.Tself + (f * a.ne + i) * 9;
+    const cx<double>* Gb = a.Gself + (f * a.ne + i) * 9;
+    for (int r = 0; r < 3; ++r) {
+      cx<R> s = mk(R(0), R(0));
+      for (int cc = 0; cc < 3; ++cc) {
+        if (useT) {
+          cx<double> d = Hb[3 * r + cc];
+          if (r == cc) d.r += 0.5;
+          s = cfma(sign * mk((R)d.r, (R)d.i), vT[cc], s);
+        }
+        if (useU) {
+          const cx<double> d = Gb[3 * r + cc];
+          s = cfma(sign * mk((R)d.r, (R)d.i), vU[cc], s);
+        }
+      }
+      o[r] = o[r] + s;
+    }
   }
   cx<R>* yo = a.y + (f * a.ne + i) * 3;
-  for (int r = 0; r < 3; ++r) yo[r] = yo[r] + o[r];
+  const double* ya = a.yacc + (f * a.ne + i) * 6;
+  for (int r = 0; r < 3; ++r) yo[r] = mk((R)ya[2 * r], (R)ya[2 * r + 1]) + o[r];
 }
 
 // ------------------------------------------------------------------------------- precond
@@ -339,42 +465,86 @@ template <class R>
 struct Cfg;
 template <>
 struct Cfg<float> {  // FP32: 128 targets x 8 frequencies per CTA, 64-element source tiles
-  static constexpr int TB = 128, S = 64, FT = 8;
+  static constexpr int TB = 128, S = 64, FT = 8, kPerSM = 4;
 };
 template <>
 struct Cfg<double> {  // FP64: 128 targets x 4 frequencies per CTA, 32-element source tiles
-  static constexpr int TB = 128, S = 32, FT = 4;
+  static constexpr int TB = 128, S = 32, FT = 4, kPerSM = 4;
 };
 
-template <class R>
-static void launch_far(bem_ctx* ctx, const cx<R>* x, cx<R>* y, int which, const int32_t* active) {
+// Device copy of the frequency list (all frequencies when `flist` is null) and the FP64
+// far-field accumulator, zeroed for the listed frequencies.
+int64_t stage_flist(bem_ctx* ctx, const std::vector<int32_t>* flist) {
+  const int64_t F = ctx->fs.F, ne = ctx->mesh.ne;
+  std::vector<int32_t>& h = ctx->flist_h;
+  if (flist) h = *flist;
+  else {
+    h.resize(F);
+    for (int64_t f = 0; f < F; ++f) h[f] = (int32_t)f;
+  }
+  const int64_t n = (int64_t)h.size();
+  ctx->flist_d.reserve(sizeof(int32_t) * std::max<int64_t>(n, 1));
+  ctx->yacc.reserve(sizeof(double) * 6 * F * ne);
+  if (n) BEM_CUDA(cudaMemcpyAsync(ctx->flist_d.p, h.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+  // zero the accumulator rows of the listed frequencies (contiguous runs in one memset each)
+  for (int64_t a = 0; a < n;) {
+    int64_t b = a + 1;
+    while (b < n && h[b] == h[b - 1] + 1) ++b;
+    BEM_CUDA(cudaMemsetAsync(ctx->yacc.as<double>() + (int64_t)h[a] * ne * 6, 0,
+                             sizeof(double) * 6 * ne * (b - a), ctx->stream));
+    a = b;
+  }
+  return n;
+}
+
+template <class R, bool RESID>
+static void launch_far(bem_ctx* ctx, const cx<R>* x, int which, int64_t nfl) {
   constexpr int TB = Cfg<R>::TB, S = Cfg<R>::S, FT = Cfg<R>::FT;
   FarArgs<R> a;
+  a.bcv = ctx->bc.set ? ctx->bc.d_value.as<double>() : nullptr;
+  a.pfac = ctx->fs.pfac.as<cx<double>>();
   a.q4 = Geo<R>::q4(ctx);
   a.cen = Geo<R>::cen(ctx);
   a.nrm = Geo<R>::nrm(ctx);
+  a.q4lo = ctx->mesh.q4_32lo.as<float4>();
+  a.cenlo = ctx->mesh.c32lo.as<float4>();
   a.bc = ctx->bc.set ? ctx->bc.d_type.as<int8_t>() : nullptr;
   a.which = which;
   a.x = x;
-  a.y = y;
+  a.yacc = ctx->yacc.as<double>();
   a.fc = Geo<R>::fc(ctx);
-  a.active = active;
+  a.flist = ctx->flist_d.as<int32_t>();
+  a.nfl = nfl;
   a.ne = ctx->mesh.ne;
   a.F = ctx->fs.F;
   a.m = Geo<R>::m(ctx);
-  const size_t smem = far_smem<R, TB, S, FT>();
-  BEM_CUDA(cudaFuncSetAttribute(far_kernel<R, TB, S, FT>,
+  // split the sources so that the grid covers about four waves of resident CTAs
+  const int64_t tb = grid_for(a.ne, TB), groups = grid_for(nfl, FT);
+  // and so that a CTA sums at most 8 source tiles in R precision before the FP64 atomic add
+  const int64_t want = 4 * 152 * Cfg<R>::kPerSM;
+  int64_t nsplit = std::max<int64_t>(1, (want + tb * groups - 1) / (tb * groups));
+  nsplit = std::max<int64_t>(nsplit, (a.ne + 8 * S - 1) / (8 * S));
+  nsplit = std::min<int64_t>(nsplit, 65535);
+  int64_t chunk = (a.ne + nsplit - 1) / nsplit;
+  chunk = ((chunk + S - 1) / S) * S;
+  nsplit = (a.ne + chunk - 1) / chunk;
+  a.chunk = chunk;
+  const size_t smem = far_smem<R, TB, S, FT, RESID>();
+  BEM_CUDA(cudaFuncSetAttribute(far_kernel<R, TB, S, FT, RESID>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const dim3 grid(grid_for(a.ne, TB), grid_for(a.F, FT));
-  ProfScope ps(ctx, sizeof(R) == 4 ? PK_FAR32 : PK_FAR64);
-  far_kernel<R, TB, S, FT><<<grid, TB, smem, ctx->stream>>>(a);
+  const dim3 grid((unsigned)tb, (unsigned)groups, (unsigned)nsplit);
+  ProfScope ps(ctx, RESID ? PK_RES64 : (sizeof(R) == 4 ? PK_FAR32 : PK_FAR64), nfl);
+  far_kernel<R, TB, S, FT, RESID><<<grid, TB, smem, ctx->stream>>>(a);
   BEM_LAUNCHED();
   ctx->launches++;
 }
 
 template <class R>
-static void launch_near(bem_ctx* ctx, const cx<R>* x, cx<R>* y, int which, const int32_t* active) {
+static void launch_near(bem_ctx* ctx, const cx<R>* x, cx<R>* y, int which, int64_t nfl, bool resid) {
   NearArgs<R> a;
+  a.resid = resid;
+  a.bcv = ctx->bc.set ? ctx->bc.d_value.as<double>() : nullptr;
+  a.pfac = ctx->fs.pfac.as<cx<double>>();
   a.q4 = Geo<R>::q4(ctx);
   a.q7 = Geo<R>::q7(ctx);
   a.cen = Geo<R>::cen(ctx);
@@ -387,28 +557,47 @@ static void launch_near(bem_ctx* ctx, const cx<R>* x, cx<R>* y, int which, const
   a.Gself = ctx->fs.Gself.as<cx<double>>();
   a.x = x;
   a.y = y;
+  a.yacc = ctx->yacc.as<double>();
   a.fc = Geo<R>::fc(ctx);
-  a.active = active;
+  a.flist = ctx->flist_d.as<int32_t>();
+  a.nfl = nfl;
   a.ne = ctx->mesh.ne;
   a.F = ctx->fs.F;
   a.m = Geo<R>::m(ctx);
-  ProfScope ps(ctx, sizeof(R) == 4 ? PK_NEAR32 : PK_NEAR64);
-  near_kernel<R><<<grid_for(a.F * a.ne, 128), 128, 0, ctx->stream>>>(a);
+  ProfScope ps(ctx, sizeof(R) == 4 ? PK_NEAR32 : PK_NEAR64, nfl);
+  near_kernel<R><<<grid_for(nfl * a.ne, 128), 128, 0, ctx->stream>>>(a);
   BEM_LAUNCHED();
   ctx->launches++;
 }
 
 void apply_operator64(bem_ctx* ctx, const cx<double>* x, cx<double>* y, int which,
-                      const int32_t* active) {
-  launch_far<double>(ctx, x, y, which, active);
-  launch_near<double>(ctx, x, y, which, active);
+                      const std::vector<int32_t>* flist) {
+  const int64_t n = stage_flist(ctx, flist);
+  if (!n) return;
+  launch_far<double, false>(ctx, x, which, n);
+  launch_near<double>(ctx, x, y, which, n, false);
+  ctx->f64_applies++;
+}
+
+void near_residual64(bem_ctx* ctx, const cx<double>* x, cx<double>* r, int64_t nfl) {
+  launch_near<double>(ctx, x, r, BEM_APPLY_A, nfl, true);
+}
+
+void residual64(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::vector<int32_t>* flist) {
+  BEM_REQUIRE(ctx->bc.set, "residual needs boundary conditions");
+  const int64_t n = stage_flist(ctx, flist);
+  if (!n) return;
+  launch_far<double, true>(ctx, x, BEM_APPLY_A, n);
+  launch_near<double>(ctx, x, r, BEM_APPLY_A, n, true);
   ctx->f64_applies++;
 }
 
 void apply_operator32(bem_ctx* ctx, const cx<float>* x, cx<float>* y, int which,
-                      const int32_t* active) {
-  launch_far<float>(ctx, x, y, which, active);
-  launch_near<float>(ctx, x, y, which, active);
+                      const std::vector<int32_t>* flist) {
+  const int64_t n = stage_flist(ctx, flist);
+  if (!n) return;
+  launch_far<float, false>(ctx, x, which, n);
+  launch_near<float>(ctx, x, y, which, n, false);
   ctx->f32_applies++;
 }
 

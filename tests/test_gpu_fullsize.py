@@ -1,0 +1,87 @@
+"""Parity at the benchmark size (5120 triangles, 128 frequencies s_k = 250 + i k pi / 0.02) in
+the launch configuration the benchmark uses, on outputs the oracle can compute one by one.
+
+* Operator: rows of A(s) x at sampled collocation points and frequencies (the oracle assembles
+  just those block-rows): FP64 path to 1e-10, FP32 path to 2e-6 relative (float-float phases).
+* Solve: the benchmark's batched mixed-precision solve of all 128 frequencies; every frequency
+  reports a certified FP64 residual <= 1e-6, and the oracle's sampled residual rows
+  r_i = b_i - (A x)_i, formed from the GPU solution, stay below 1e-6 ||b||.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import bem as OB
+
+pytestmark = pytest.mark.gpu
+
+ROWS = np.array([0, 777, 2048, 3333, 5119])
+KS = np.array([0, 37, 90, 127])
+
+
+@functools.lru_cache(maxsize=None)
+def _problem():
+    prob = W.spherical_cavity(level=4, n_freq=128)
+    return prob, OB.geometry(prob.verts, prob.tris)
+
+
+def _ctx():
+    import paper_1511_04355_gb300 as P
+    prob, _ = _problem()
+    c = P.Context(0)
+    c.set_mesh(prob.verts, prob.tris)
+    m = prob.material
+    c.set_material(m.mu, m.nu, m.rho)
+    c.set_bc(prob.bc_type, prob.bc_value, P.BEM_PROFILE_STEP)
+    return c
+
+
+def _rows(idx):
+    return np.concatenate([[3 * i, 3 * i + 1, 3 * i + 2] for i in idx])
+
+
+def test_operator_rows_full_size():
+    import torch
+    import paper_1511_04355_gb300 as P
+    prob, g = _problem()
+    c = _ctx()
+    ne = len(prob.tris)
+    x = W.random_complex_vectors(128, 3 * ne, seed=5)
+    xd = torch.from_numpy(x).cuda()
+    y64 = torch.zeros_like(xd)
+    y32 = torch.zeros_like(xd)
+    P.bem_apply(c.h, prob.s, xd, y64, P.BEM_PREC_FP64, P.BEM_APPLY_A)
+    P.bem_apply(c.h, prob.s, xd, y32, P.BEM_PREC_FP32, P.BEM_APPLY_A)
+    y64, y32 = y64.cpu().numpy(), y32.cpu().numpy()
+    rr = _rows(ROWS)
+    for k in KS:
+        A, _ = OB.operators(g, prob.s[k], prob.material, prob.bc_type, rows=ROWS)
+        ref = A @ x[k]
+        scale = np.abs(ref).max()
+        assert np.abs(y64[k, rr] - ref).max() <= 1e-10 * scale, k
+        assert np.abs(y32[k, rr] - ref).max() <= 2e-6 * scale, (k, np.abs(y32[k, rr] - ref).max() / scale)
+
+
+def test_benchmark_solve_residuals():
+    import torch
+    import paper_1511_04355_gb300 as P
+    prob, g = _problem()
+    c = _ctx()
+    c.set_options(precision=P.BEM_PREC_MIXED, tol=1e-6)
+    ne = len(prob.tris)
+    sd = torch.from_numpy(prob.s).cuda()
+    xd = torch.zeros((128, 3 * ne), dtype=torch.complex128, device="cuda")
+    _, info = P.bem_solve_frequencies(c.h, sd, xd)
+    assert (info["status"] == 0).all()
+    assert (info["residual"] <= 1e-6).all()
+    x = xd.cpu().numpy()
+    b = c.rhs(prob.s[KS])
+    rr = _rows(ROWS)
+    for j, k in enumerate(KS):
+        A, Kn = OB.operators(g, prob.s[k], prob.material, prob.bc_type, rows=ROWS)
+        b_rows = Kn @ OB.known_data(prob.bc_value, prob.s[k])
+        assert np.abs(b[j, rr] - b_rows).max() <= 1e-10 * np.abs(b_rows).max()
+        r_rows = b_rows - A @ x[k]
+        assert np.abs(r_rows).max() <= 1e-6 * np.linalg.norm(b[j]), k

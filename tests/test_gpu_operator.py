@@ -137,3 +137,38 @@ def test_invalid_arguments_are_errors():
     with pytest.raises(P.BemError) as e:
         c2.rhs(np.array([250.0]))
     assert e.value.code in (P.BEM_ERR_NO_MESH, P.BEM_ERR_INVALID_ARG)
+
+
+@pytest.mark.parametrize("level,mixed_bc", [(1, False), (2, False), (2, True)])
+def test_refinement_residual_df64_and_fp64(level, mixed_bc):
+    """r = b - A x: the float-float far field (default in the mixed solver) and the native FP64
+    one both match the oracle's dense b - A x; at a near-solution x (residual ~1e-6 ||b||, the
+    regime the refinement certifies) the float-float residual stays within 1e-10 ||b|| (measured
+    ~2e-11: float-float precision times the cancellation of the sum), 1e4 below the tolerance."""
+    P = _P()
+    v, f, m, bc, val, g, ops = _case(level, mixed_bc)
+    c = _ctx(level, mixed_bc)
+    x = W.random_complex_vectors(len(S_SET), 3 * len(f), seed=21) * 1e-6
+    for mode in (P.BEM_RESID_DF64, P.BEM_RESID_FP64):
+        r = c.residual(S_SET, x, mode)
+        for k, s in enumerate(S_SET):
+            A, Kn = ops[k]
+            b = Kn @ OB.known_data(val, s)
+            ref = b - A @ x[k]
+            assert np.abs(r[k] - ref).max() <= 1e-10 * np.abs(ref).max(), (mode, k)
+    # near-solution: x = A^{-1} b (1 + 1e-6 noise)
+    rng = np.random.default_rng(3)
+    xs = []
+    for k, s in enumerate(S_SET):
+        A, Kn = ops[k]
+        b = Kn @ OB.known_data(val, s)
+        xe = np.linalg.solve(A, b)
+        # entrywise relative noise: the unknowns mix displacements and tractions
+        xs.append(xe * (1 + 1e-6 * (rng.standard_normal(len(xe)) + 1j * rng.standard_normal(len(xe)))))
+    xs = np.array(xs)
+    r = c.residual(S_SET, xs, P.BEM_RESID_DF64)
+    for k, s in enumerate(S_SET):
+        A, Kn = ops[k]
+        b = Kn @ OB.known_data(val, s)
+        ref = b - A @ xs[k]
+        assert np.linalg.norm(r[k] - ref) <= 1e-10 * np.linalg.norm(b), k
