@@ -1,0 +1,98 @@
+"""Pins of the oracle's vector fitting (Sec. 2.3) and adaptive frequency sampling (Sec. 3).
+
+* VF recovers the poles and residues of a known rational function exactly (to rounding) and an
+  over-ordered fit reproduces the data; the time response of r/(s - a) is r e^{a t} (the sign of
+  Eq. (vf-td) is read this way) -- checked on 1/(s + a) = L{e^{-a t}}.
+* VF on the closed-form spherical-cavity response finds its physical pole pair.
+* AFS on a rational response converges with fewer samples than the poles' FSM grid would need
+  and returns the exact transient; on the cavity closed form it returns the exact u_r(t).
+* The Chebyshev initial set and the fit orders follow their formulas.
+"""
+import math
+
+import numpy as np
+
+import workloads as W
+from oracle import afs, closed_form as CF, fsm, vf
+
+MODES = np.array([-40 + 400j, -60 + 1100j, -90 + 2300j, -120 + 3700j, -150 + 5200j])
+
+
+def _rational(K=6, seed=1, real_pole=0.0):
+    rng = np.random.default_rng(seed)
+    poles = np.concatenate([MODES, np.conj(MODES), [real_pole + 0j]])
+    R = rng.standard_normal((K, len(MODES))) + 1j * rng.standard_normal((K, len(MODES)))
+    Rf = np.hstack([R, np.conj(R), rng.standard_normal((K, 1)) + 0j])
+    return poles, Rf
+
+
+def test_vf_recovers_known_poles_and_residues():
+    poles, R = _rational(real_pole=-300.0)
+    s = 250 + 1j * np.linspace(0, 6000, 60)
+    F = vf.evaluate(s, poles, R)
+    p, Rr = vf.fit(s, F[:, :3], 11, 6000.0)
+    order = np.argsort(p.imag + 1e-9 * p.real)
+    ref = np.argsort(poles.imag + 1e-9 * poles.real)
+    assert np.abs(p[order] - poles[ref]).max() < 1e-8 * np.abs(poles).max()
+    # residues of all six responses with the poles identified from the first three
+    pairs = p[p.imag > 0]
+    reals = p[np.abs(p.imag) == 0].real
+    p2, R2 = vf.residues(s, F, pairs, reals)
+    assert np.abs(vf.evaluate(s, p2, R2) - F).max() < 1e-10 * np.abs(F).max()
+
+
+def test_vf_overordered_fit_reproduces_data():
+    poles, R = _rational(real_pole=-300.0)
+    s = 250 + 1j * np.linspace(0, 6000, 60)
+    F = vf.evaluate(s, poles, R)
+    p, Rr = vf.fit(s, F, 17, 6000.0)
+    assert np.abs(vf.evaluate(s, p, Rr) - F).max() < 1e-9 * np.abs(F).max()
+
+
+def test_time_response_sign():
+    a = 300.0
+    t = np.linspace(0, 0.01, 11)
+    h = vf.time_response(t, np.array([-a + 0j]), np.array([[1.0 + 0j]]))
+    assert np.abs(h[:, 0] - np.exp(-a * t)).max() < 1e-15
+
+
+def test_vf_on_cavity_closed_form():
+    m = W.CAVITY_MATERIAL
+    s = W.fsm_frequencies(0.02, 250.0, 64)
+    F = CF.cavity_ur(s, 1.0, m.mu, m.nu, m.rho, W.CAVITY_P0)[:, None]
+    p, Rr = vf.fit(s, F, 5, s[-1].imag)
+    true_p, _ = CF.cavity_poles_residues(1.0, m.mu, m.nu, m.rho, W.CAVITY_P0)
+    pair = true_p[true_p.imag > 0][0]
+    assert np.abs(p - pair).min() < 1e-8 * abs(pair)
+    assert np.abs(vf.evaluate(s, p, Rr) - F).max() < 1e-10 * np.abs(F).max()
+
+
+def test_chebyshev_initial_set_and_fit_orders():
+    s = afs.chebyshev_frequencies(250.0, 1000.0, 16)
+    assert np.allclose(s.real, 250.0)
+    assert abs(s[0].imag) < 1e-12 and abs(s[-1].imag - 1000.0) < 1e-9
+    assert np.all(np.diff(s.imag) > 0)
+    assert afs.fit_orders(30) == (15, 13)
+    assert afs.fit_orders(16) == (8, 6)
+
+
+def test_afs_on_rational_response_is_exact():
+    poles, R = _rational()
+    T = 0.04
+    eta = 3 * math.log(10) / T
+    res = afs.run(lambda s: vf.evaluate(s, poles, R), eta, 6000.0, T, orf=[0, 1, 2, 3],
+                  test=[4, 5], J0=8)
+    exact = vf.time_response(res.t, poles, R)
+    assert np.abs(res.h - exact).max() < 1e-9 * np.abs(exact).max()
+    # an FSM of the same band with the same period needs Omega T / pi + 1 = 77 solves
+    assert len(res.s) < 6000.0 * T / math.pi + 1
+    assert res.E1[-1] < 1e-4 and res.E2[-1] < 2e-3
+
+
+def test_afs_on_cavity_closed_form():
+    m = W.CAVITY_MATERIAL
+    ur = lambda s: np.repeat(CF.cavity_ur(s, 1.0, m.mu, m.nu, m.rho, W.CAVITY_P0)[:, None], 2, axis=1)
+    res = afs.run(ur, 250.0, 63 * math.pi / 0.02, 0.02, orf=[0], test=[1], J0=8)
+    ex = CF.cavity_ur_time(res.t, 1.0, m.mu, m.nu, m.rho, W.CAVITY_P0)
+    assert np.abs(res.h[:, 1] - ex).max() < 1e-8 * np.abs(ex).max()
+    assert len(res.s) < 64
