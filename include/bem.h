@@ -194,6 +194,73 @@ int bem_fsm_eval_noalloc(const double* h, int64_t nc, int64_t m, double eta, dou
                          const double* t, int64_t nt, int window, double* out, void* cuda_stream);
 const char* bem_noalloc_last_error(void);
 
+/* ------------------------------------------------------------------ vector fitting + AFS */
+
+/* Vector fit (step a10; Sec. 2.3, Eq. (vf-f)) on the host, FP64: f_k(s) ~ sum_m r_km/(s - a_m)
+ * with common poles, fitted to K responses sampled at J frequencies.  Pole identification uses
+ * the responses listed in fit_cols (NULL = all), starting from pairs -b/100 +- i b with b
+ * equally spaced over (0, omega_max] (and -omega_max/100 when M is odd), n_iter relocations
+ * (stopping early when the poles move less than 1e-10 omega_max); unstable poles are kept.
+ * s: J complex (host); F: J x K complex row-major (host).  Outputs (host): poles[M] complex,
+ * conjugate pairs adjacent; residues[K x M] complex.  Errors (bem_last_error(NULL)):
+ * INVALID_ARG (M > J, sizes), BREAKDOWN (eigenvalue iteration failed). */
+int bem_vf_fit(const double* s, int64_t J, const double* F, int64_t K, const int32_t* fit_cols,
+               int32_t n_fit_cols, int32_t M, double omega_max, int32_t n_iter, double* poles,
+               double* residues);
+/* The fitted responses at n complex frequencies: out[n x K] complex (host). */
+int bem_vf_eval(const double* poles, int32_t M, const double* residues, int64_t K, const double* s,
+                int64_t n, double* out);
+/* Time responses, Eq. (vf-td): out[nt x K] = sum over poles with Re a_m < eta of r_km e^{a_m t}
+ * (the inverse Laplace transform of r/(s - a) is r e^{a t}; the printed exponent sign is read
+ * as a misprint).  eta: abscissa of the line the samples were taken on -- the Bromwich contour
+ * of Eq. (invLap) collects the residues of the poles to its left only; pass +inf to sum all. */
+int bem_vf_time(const double* poles, int32_t M, const double* residues, int64_t K, const double* t,
+                int64_t nt, double eta, double* out);
+
+typedef struct bem_afs_params {
+  double eta;        /* Re s of every sample (Sec. 2.2: eta = kappa ln(10) / T)          */
+  double omega_max;  /* frequency band [0, Omega_s]                                       */
+  double T;          /* time window of the E1 integrals (Eq. (stop-E1))                   */
+  double alpha_H, alpha_L; /* fit orders M = floor(J / alpha) (Eq. (fit-ords); 2.0, 2.3) */
+  double E1bar, E2bar;     /* convergence thresholds (Eq. (converge); 1e-4, 2e-3)        */
+  int32_t J0;        /* initial Chebyshev frequencies (16)                                */
+  int32_t Jc;        /* validation steps after the first converged one (3)                */
+  int32_t n_grid;    /* uniform search grid for s_new over [0, Omega_s] (4096)            */
+  int32_t nt;        /* time points of the E1 integrals (512)                             */
+  int32_t max_samples; /* cap on N_c (400)                                                */
+  int32_t vf_iters;  /* pole relocations per fit (20)                                     */
+  int32_t reserved[6];
+} bem_afs_params;
+
+typedef struct bem_afs_stats {
+  int64_t capacity;  /* in: entries available in each array below                          */
+  double* s;         /* [capacity] complex: sampled frequencies in sampling order (null.) */
+  int32_t* gmres_iters; /* [capacity] GMRES iterations of each sample's solve (nullable)   */
+  double* E1;        /* [capacity] E1 per AFS step (nullable)                             */
+  double* E2;        /* [capacity] E2 per AFS step (nullable)                             */
+  double* poles;     /* [capacity] complex: poles of the final M_H fit (nullable)         */
+  int64_t n_samples; /* out: N_c                                                          */
+  int64_t n_steps;   /* out: AFS steps (entries written to E1 / E2)                       */
+  int32_t n_poles;   /* out: order of the final fit                                       */
+  double seconds_solve, seconds_fit; /* out: time in BEM solves / in fitting             */
+} bem_afs_stats;
+
+/* Fill *p with the paper's parameter values (Sec. 3.4) and the defaults above; eta,
+ * omega_max and T must still be set. */
+int bem_default_afs_params(bem_afs_params* p);
+
+/* Adaptive frequency sampling (Sec. 3, Algorithm AFS): starting from J0 Chebyshev frequencies,
+ * repeatedly fits the observation responses (ORFs: unknowns orf[K]) at two orders, solves the
+ * BEM system (one batched GPU solve, the context's options) at the frequency where the fits
+ * disagree most, and stops when the time-domain change E1 and the fit discrepancy E2 of the
+ * test unknowns test[Kt] stay below their thresholds for Jc + 1 consecutive steps.
+ * resp_out[nt_out x (K + Kt)] (host or device): time responses of the ORFs then the test
+ * unknowns at t_out[nt_out] (Eq. (vf-td), final fit); stats nullable.
+ * Errors: INVALID_ARG, NOT_CONVERGED (a frequency solve failed), NO_MESH, CUDA. */
+int bem_afs(bem_ctx* ctx, const bem_afs_params* params, const int64_t* orf, int64_t K,
+            const int64_t* test, int64_t Kt, const double* t_out, int64_t nt_out, double* resp_out,
+            bem_afs_stats* stats);
+
 /* ------------------------------------------------------------------ operator-level calls
  * (the steps of one solve, exposed for verification and measurement) */
 

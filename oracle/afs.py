@@ -17,6 +17,8 @@ Sec. 3 of the paper (Algorithm AFS), written over a callback `solve(s_list) -> r
   convergence     stop once E1 < E1bar and E2 < E2bar hold at a step and at the J_c steps that
                   follow (Eq. (converge) with the validation stage);
   post-processing time responses by Eq. (vf-td) with the final M_H fit.
+Time responses (for E1 and the output) sum Eq. (vf-td) over the fitted poles left of the
+sampling line Re s = eta only (the Bromwich contour of Eq. (invLap)); see vf.time_response.
 Readings where the paper is silent: the search for s_new runs over n_grid uniform frequencies in
 [0, Omega] and skips grid points within 1.5 grid spacings of an existing sample; each ORF is
 scaled by its largest sampled magnitude before pole identification; the integrals of E1 are
@@ -71,7 +73,7 @@ def _step(s, F, orf, eta, omega_max, grid, t, alpha_H, alpha_L, n_iter):
     fL = vf.evaluate(grid, polesL, RL)
     diff = np.abs(fH - fL)
     e = diff.max(axis=0) / np.maximum(np.abs(fH).max(axis=0), 1e-300)
-    h = vf.time_response(t, polesH, RH)
+    h = vf.time_response(t, polesH, RH, eta)
     return polesH, RH, e, diff, h
 
 

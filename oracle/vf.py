@@ -143,7 +143,15 @@ def evaluate(s, poles, R):
     return (1.0 / (s - poles[None, :])) @ R.T
 
 
-def time_response(t, poles, R):
-    """Eq. (vf-td): h(t) = sum_m r_m e^{a_m t}, real part (conjugate pairs sum to real)."""
+def time_response(t, poles, R, eta=None):
+    """Eq. (vf-td): h(t) = sum_m r_m e^{a_m t}, real part (conjugate pairs sum to real).
+
+    With eta given, the sum runs over the poles left of the sampling line Re s = eta only: the
+    Bromwich integral of Eq. (invLap) along that line -- the contour the samples lie on, which
+    Sec. 2.2 places to the right of every singularity -- picks up exactly those residues; a
+    fitted pole right of the line lies outside the region the data describe."""
     t = np.asarray(t)[:, None]
+    if eta is not None:
+        keep = poles.real < eta
+        poles, R = poles[keep], R[:, keep]
     return np.real(np.exp(t * poles[None, :]) @ R.T)

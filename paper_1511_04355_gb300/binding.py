@@ -69,6 +69,22 @@ class bem_solve_stats(C.Structure):
                 ("fp64_operator_applies", C.c_int64), ("kernel_launches", C.c_int64)]
 
 
+class bem_afs_params(C.Structure):
+    _fields_ = [("eta", C.c_double), ("omega_max", C.c_double), ("T", C.c_double),
+                ("alpha_H", C.c_double), ("alpha_L", C.c_double), ("E1bar", C.c_double),
+                ("E2bar", C.c_double), ("J0", C.c_int32), ("Jc", C.c_int32), ("n_grid", C.c_int32),
+                ("nt", C.c_int32), ("max_samples", C.c_int32), ("vf_iters", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
+
+
+class bem_afs_stats(C.Structure):
+    _fields_ = [("capacity", C.c_int64), ("s", C.POINTER(C.c_double)),
+                ("gmres_iters", C.POINTER(C.c_int32)), ("E1", C.POINTER(C.c_double)),
+                ("E2", C.POINTER(C.c_double)), ("poles", C.POINTER(C.c_double)),
+                ("n_samples", C.c_int64), ("n_steps", C.c_int64), ("n_poles", C.c_int32),
+                ("seconds_solve", C.c_double), ("seconds_fit", C.c_double)]
+
+
 _P = C.c_void_p
 _I64 = C.c_int64
 _SIGS = {
@@ -89,6 +105,12 @@ _SIGS = {
     "bem_precond_apply": (C.c_int, [_P, _P, _I64, _P, _P]),
     "bem_residual": (C.c_int, [_P, _P, _I64, _P, _P, C.c_int]),
     "bem_profile": (C.c_int, [_P, C.c_int]),
+    "bem_vf_fit": (C.c_int, [_P, _I64, _P, _I64, _P, C.c_int32, C.c_int32, C.c_double, C.c_int32, _P, _P]),
+    "bem_vf_eval": (C.c_int, [_P, C.c_int32, _P, _I64, _P, _I64, _P]),
+    "bem_vf_time": (C.c_int, [_P, C.c_int32, _P, _I64, _P, _I64, C.c_double, _P]),
+    "bem_default_afs_params": (C.c_int, [C.POINTER(bem_afs_params)]),
+    "bem_afs": (C.c_int, [_P, C.POINTER(bem_afs_params), _P, _I64, _P, _I64, _P, _I64, _P,
+                          C.POINTER(bem_afs_stats)]),
     "bem_fsm_eval": (C.c_int, [_P, _P, _I64, _I64, C.c_double, C.c_double, _P, _I64, C.c_int, _P]),
     "bem_fsm_eval_noalloc": (C.c_int, [_P, _I64, _I64, C.c_double, C.c_double, _P, _I64, C.c_int,
                                        _P, _P]),
@@ -336,6 +358,80 @@ def bem_fsm(ctx, period, eta, nc, t, dofs, allow_not_converged=False):
     return out, arr
 
 
+def _check_global(rc, what):
+    if rc != BEM_OK:
+        msg = load_library().bem_last_error(None)
+        raise BemError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+
+def bem_vf_fit(s, F, M, omega_max, n_iter=20, fit_cols=None):
+    """Vector fit (host, FP64).  s (J,), F (J, K) complex -> (poles (M,), residues (K, M))."""
+    s = np.ascontiguousarray(s, dtype=np.complex128).reshape(-1)
+    F = np.ascontiguousarray(F, dtype=np.complex128).reshape(len(s), -1)
+    K = F.shape[1]
+    cols = None if fit_cols is None else np.ascontiguousarray(fit_cols, dtype=np.int32)
+    poles = np.zeros(M, np.complex128)
+    R = np.zeros((K, M), np.complex128)
+    rc = load_library().bem_vf_fit(_ptr(s), len(s), _ptr(F), K, _ptr(cols),
+                                   0 if cols is None else len(cols), M, omega_max, n_iter,
+                                   _ptr(poles), _ptr(R))
+    _check_global(rc, "bem_vf_fit")
+    return poles, R
+
+
+def bem_vf_eval(poles, R, s):
+    poles = np.ascontiguousarray(poles, dtype=np.complex128)
+    R = np.ascontiguousarray(R, dtype=np.complex128)
+    s = np.ascontiguousarray(s, dtype=np.complex128).reshape(-1)
+    out = np.zeros((len(s), R.shape[0]), np.complex128)
+    _check_global(load_library().bem_vf_eval(_ptr(poles), len(poles), _ptr(R), R.shape[0], _ptr(s),
+                                             len(s), _ptr(out)), "bem_vf_eval")
+    return out
+
+
+def bem_vf_time(poles, R, t, eta=float("inf")):
+    poles = np.ascontiguousarray(poles, dtype=np.complex128)
+    R = np.ascontiguousarray(R, dtype=np.complex128)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    out = np.zeros((len(t), R.shape[0]), np.float64)
+    _check_global(load_library().bem_vf_time(_ptr(poles), len(poles), _ptr(R), R.shape[0], _ptr(t),
+                                             len(t), eta, _ptr(out)), "bem_vf_time")
+    return out
+
+
+def bem_default_afs_params(**kw):
+    p = bem_afs_params()
+    load_library().bem_default_afs_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def bem_afs(ctx, params, orf, test, t_out, capacity=1024):
+    """Adaptive frequency sampling; returns (responses (nt, K + Kt), stats dict)."""
+    orf = np.ascontiguousarray(orf, dtype=np.int64)
+    test = np.ascontiguousarray(test, dtype=np.int64)
+    t_out = np.ascontiguousarray(t_out, dtype=np.float64)
+    out = np.zeros((len(t_out), len(orf) + len(test)), np.float64)
+    st = bem_afs_stats()
+    st.capacity = capacity
+    arr = dict(s=np.zeros(capacity, np.complex128), gmres_iters=np.zeros(capacity, np.int32),
+               E1=np.zeros(capacity), E2=np.zeros(capacity), poles=np.zeros(capacity, np.complex128))
+    st.s = arr["s"].ctypes.data_as(C.POINTER(C.c_double))
+    st.gmres_iters = arr["gmres_iters"].ctypes.data_as(C.POINTER(C.c_int32))
+    st.E1 = arr["E1"].ctypes.data_as(C.POINTER(C.c_double))
+    st.E2 = arr["E2"].ctypes.data_as(C.POINTER(C.c_double))
+    st.poles = arr["poles"].ctypes.data_as(C.POINTER(C.c_double))
+    rc = load_library().bem_afs(ctx, C.byref(params), _ptr(orf), len(orf), _ptr(test), len(test),
+                                _ptr(t_out), len(t_out), _ptr(out), C.byref(st))
+    _check(ctx, rc, "bem_afs")
+    n, ns, npol = st.n_samples, st.n_steps, st.n_poles
+    info = dict(s=arr["s"][:n], gmres_iters=arr["gmres_iters"][:n], E1=arr["E1"][:ns],
+                E2=arr["E2"][:ns], poles=arr["poles"][:npol], n_samples=n,
+                seconds_solve=st.seconds_solve, seconds_fit=st.seconds_fit)
+    return out, info
+
+
 def bem_profile(ctx, enable=True):
     _check(ctx, load_library().bem_profile(ctx, 1 if enable else 0), "bem_profile")
 
@@ -412,6 +508,9 @@ class Context:
 
     def fsm_eval(self, h, eta, period, t, window=1):
         return bem_fsm_eval(self.h, h, eta, period, t, window)
+
+    def afs(self, params, orf, test, t_out):
+        return bem_afs(self.h, params, orf, test, t_out)
 
     def fsm(self, period, eta, nc, t, dofs, allow_not_converged=False):
         return bem_fsm(self.h, period, eta, nc, t, dofs, allow_not_converged)

@@ -99,19 +99,7 @@ std::string g_create_err;
 
 template <class Fn>
 int guarded(bem_ctx* ctx, Fn&& fn) {
-  try {
-    if (!ctx) throw Error(BEM_ERR_INVALID_ARG, "null context");
-    BEM_CUDA(cudaSetDevice(ctx->device));
-    ctx->launches = 0;
-    fn();
-    return BEM_OK;
-  } catch (const Error& e) {
-    if (ctx) ctx->err = e.what();
-    return e.code;
-  } catch (const std::exception& e) {
-    if (ctx) ctx->err = e.what();
-    return BEM_ERR_INVALID_ARG;
-  }
+  return guarded_call(ctx, std::forward<Fn>(fn));
 }
 
 void need_mesh(bem_ctx* ctx) {
@@ -123,6 +111,17 @@ void need_bc(bem_ctx* ctx) {
   if (!ctx->bc.set) throw Error(BEM_ERR_INVALID_ARG, "bem_set_bc has not been called");
 }
 }  // namespace
+
+namespace bem {
+void set_global_error(const std::string& m) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_create_err = m;
+}
+void need_problem(bem_ctx* ctx) {
+  need_mesh(ctx);
+  need_bc(ctx);
+}
+}  // namespace bem
 
 extern "C" {
 

@@ -295,6 +295,26 @@ void fsm_launch(const cx<double>* h, int64_t nc, int64_t m, double eta, double p
 void gather_dofs(bem_ctx* ctx, const cx<double>* x, int64_t N, int64_t F, const int64_t* dofs_dev,
                  int64_t nd, cx<double>* out);
 
+// error handling shared by the entry points: runs fn, turns exceptions into codes + messages
+void set_global_error(const std::string& m);
+template <class Fn>
+int guarded_call(bem_ctx* ctx, Fn&& fn) {
+  try {
+    if (!ctx) throw Error(BEM_ERR_INVALID_ARG, "null context");
+    BEM_CUDA(cudaSetDevice(ctx->device));
+    ctx->launches = 0;
+    fn();
+    return BEM_OK;
+  } catch (const Error& e) {
+    if (ctx) ctx->err = e.what();
+    return e.code;
+  } catch (const std::exception& e) {
+    if (ctx) ctx->err = e.what();
+    return BEM_ERR_INVALID_ARG;
+  }
+}
+void need_problem(bem_ctx* ctx);  // mesh, material and boundary conditions set
+
 // helpers
 inline int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }
 bool is_device_ptr(const void* p);
