@@ -194,6 +194,51 @@ int bem_fsm_eval_noalloc(const double* h, int64_t nc, int64_t m, double eta, dou
                          const double* t, int64_t nt, int window, double* out, void* cuda_stream);
 const char* bem_noalloc_last_error(void);
 
+/* ------------------------------------------------------------------ learned warm start (a8) */
+
+/* The warm start gives each new frequency solve an initial guess built from solutions already
+ * computed (the paper's adaptive sampling solves one new frequency at a time next to solved
+ * ones; the warm start itself is not in the paper).  BEM_WARM_NEAREST: the stored solution at
+ * the nearest stored frequency.  BEM_WARM_MLP: x0(s) = Phi c(s), Phi = the leading left singular
+ * vectors (POD) of the stored solutions, c(s) predicted by a 2 -> 128 -> 128 -> 2r MLP (tanh-GELU)
+ * trained on the stored (s, Phi^H x) pairs; its dense layers run on the tensor cores (FP16
+ * operands, FP32 accumulation), the rest in FP32.  The GMRES tolerance is unchanged, so the
+ * warm start changes the iteration count, never the accepted accuracy. */
+typedef struct bem_warm_params {
+  int32_t r_max;    /* POD rank cap (32)                                               */
+  double rel_tol;   /* keep singular values > rel_tol * sigma_1 (1e-10)                */
+  int32_t steps;    /* Adam steps (2000)                                               */
+  double lr;        /* Adam learning rate (1e-3; beta1 0.9, beta2 0.999, eps 1e-8)      */
+  uint64_t seed;    /* weight initialisation (uniform +-1/sqrt(fan_in), zero biases)    */
+  int32_t reserved[4];
+} bem_warm_params;
+
+typedef struct bem_warm_stats {
+  int32_t r;             /* out: POD rank                                    */
+  int32_t n_snapshots;   /* out: stored solutions used                       */
+  double loss_first, loss_last; /* out: training loss at the first/last step */
+  double seconds;        /* out                                              */
+} bem_warm_stats;
+
+int bem_default_warm_params(bem_warm_params* p);
+
+/* Add ns solutions x[ns x 3ne] complex (host or device) at frequencies s[ns] (host) to the
+ * context's warm-start memory (FP64 device copies; at most 256 are used for training). */
+int bem_warm_store(bem_ctx* ctx, const double* s, int64_t ns, const double* x);
+/* Forget every stored solution and the trained model. */
+int bem_warm_clear(bem_ctx* ctx);
+/* POD of the stored solutions, then MLP training on the device.  stats nullable.
+ * Errors: INVALID_ARG (fewer than 2 or more than 256 stored solutions). */
+int bem_warm_train(bem_ctx* ctx, const bem_warm_params* p, bem_warm_stats* stats);
+/* The trained POD basis: phi[r x 3ne] complex (host or device, NULL to query r). */
+int bem_warm_basis(bem_ctx* ctx, double* phi, int32_t* r);
+/* One MLP pass with caller parameters (verification): params (host, float, the layout
+ * W1[128x2], b1[128], W2[128x128], b2[128], W3[2r x 128], b3[2r], row-major), inputs U[B x 2],
+ * targets T[B x 2r] (nullable: forward only).  Outputs (host): y[B x 2r]; grads[nparams] and
+ * *loss (L = sum |y - T|^2 / (2B)) when T is given. */
+int bem_mlp_eval(bem_ctx* ctx, int32_t r, const float* params, const float* U, int32_t B,
+                 const float* T, float* y, float* grads, double* loss);
+
 /* ------------------------------------------------------------------ vector fitting + AFS */
 
 /* Vector fit (step a10; Sec. 2.3, Eq. (vf-f)) on the host, FP64: f_k(s) ~ sum_m r_km/(s - a_m)

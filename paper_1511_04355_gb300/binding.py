@@ -85,6 +85,16 @@ class bem_afs_stats(C.Structure):
                 ("seconds_solve", C.c_double), ("seconds_fit", C.c_double)]
 
 
+class bem_warm_params(C.Structure):
+    _fields_ = [("r_max", C.c_int32), ("rel_tol", C.c_double), ("steps", C.c_int32),
+                ("lr", C.c_double), ("seed", C.c_uint64), ("reserved", C.c_int32 * 4)]
+
+
+class bem_warm_stats(C.Structure):
+    _fields_ = [("r", C.c_int32), ("n_snapshots", C.c_int32), ("loss_first", C.c_double),
+                ("loss_last", C.c_double), ("seconds", C.c_double)]
+
+
 _P = C.c_void_p
 _I64 = C.c_int64
 _SIGS = {
@@ -105,6 +115,12 @@ _SIGS = {
     "bem_precond_apply": (C.c_int, [_P, _P, _I64, _P, _P]),
     "bem_residual": (C.c_int, [_P, _P, _I64, _P, _P, C.c_int]),
     "bem_profile": (C.c_int, [_P, C.c_int]),
+    "bem_default_warm_params": (C.c_int, [C.POINTER(bem_warm_params)]),
+    "bem_warm_store": (C.c_int, [_P, _P, _I64, _P]),
+    "bem_warm_clear": (C.c_int, [_P]),
+    "bem_warm_train": (C.c_int, [_P, C.POINTER(bem_warm_params), C.POINTER(bem_warm_stats)]),
+    "bem_warm_basis": (C.c_int, [_P, _P, C.POINTER(C.c_int32)]),
+    "bem_mlp_eval": (C.c_int, [_P, C.c_int32, _P, _P, C.c_int32, _P, _P, _P, C.POINTER(C.c_double)]),
     "bem_vf_fit": (C.c_int, [_P, _I64, _P, _I64, _P, C.c_int32, C.c_int32, C.c_double, C.c_int32, _P, _P]),
     "bem_vf_eval": (C.c_int, [_P, C.c_int32, _P, _I64, _P, _I64, _P]),
     "bem_vf_time": (C.c_int, [_P, C.c_int32, _P, _I64, _P, _I64, C.c_double, _P]),
@@ -430,6 +446,57 @@ def bem_afs(ctx, params, orf, test, t_out, capacity=1024):
                 E2=arr["E2"][:ns], poles=arr["poles"][:npol], n_samples=n,
                 seconds_solve=st.seconds_solve, seconds_fit=st.seconds_fit)
     return out, info
+
+
+def bem_default_warm_params(**kw):
+    p = bem_warm_params()
+    load_library().bem_default_warm_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def bem_warm_store(ctx, s, x):
+    s, ns = _cplx_as_pairs(s)
+    if isinstance(x, np.ndarray):
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+    _check(ctx, load_library().bem_warm_store(ctx, _ptr(s), ns, _ptr(x)), "bem_warm_store")
+
+
+def bem_warm_clear(ctx):
+    _check(ctx, load_library().bem_warm_clear(ctx), "bem_warm_clear")
+
+
+def bem_warm_train(ctx, params=None):
+    params = params or bem_default_warm_params()
+    st = bem_warm_stats()
+    _check(ctx, load_library().bem_warm_train(ctx, C.byref(params), C.byref(st)), "bem_warm_train")
+    return dict(r=st.r, n_snapshots=st.n_snapshots, loss_first=st.loss_first, loss_last=st.loss_last,
+                seconds=st.seconds)
+
+
+def bem_warm_basis(ctx, n_unknowns):
+    r = C.c_int32()
+    _check(ctx, load_library().bem_warm_basis(ctx, None, C.byref(r)), "bem_warm_basis")
+    phi = np.zeros((r.value, n_unknowns), np.complex128)
+    _check(ctx, load_library().bem_warm_basis(ctx, _ptr(phi), C.byref(r)), "bem_warm_basis")
+    return phi
+
+
+def bem_mlp_eval(ctx, r, params, U, T=None):
+    """(y, grads, loss) of one MLP pass with the given flat float32 parameters."""
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    U = np.ascontiguousarray(U, dtype=np.float32)
+    B = U.shape[0]
+    y = np.zeros((B, 2 * r), np.float32)
+    grads = None
+    loss = C.c_double(0.0)
+    if T is not None:
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        grads = np.zeros_like(params)
+    _check(ctx, load_library().bem_mlp_eval(ctx, r, _ptr(params), _ptr(U), B, _ptr(T), _ptr(y),
+                                            _ptr(grads), C.byref(loss)), "bem_mlp_eval")
+    return y, grads, loss.value
 
 
 def bem_profile(ctx, enable=True):

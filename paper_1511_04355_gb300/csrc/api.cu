@@ -371,6 +371,59 @@ int bem_rhs(bem_ctx* ctx, const double* s, int64_t ns, double* b_out) {
   });
 }
 
+int bem_default_warm_params(bem_warm_params* p) {
+  if (!p) return BEM_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof *p);
+  p->r_max = 32;
+  p->rel_tol = 1e-10;
+  p->steps = 2000;
+  p->lr = 1e-3;
+  p->seed = 20151113ull;
+  return BEM_OK;
+}
+
+int bem_warm_store(bem_ctx* ctx, const double* s, int64_t ns, const double* x) {
+  return guarded(ctx, [&] {
+    if (ctx->mesh.ne <= 0) throw Error(BEM_ERR_NO_MESH, "bem_set_mesh has not been called");
+    BEM_REQUIRE(s && x && ns >= 1, "bad argument");
+    warm_store(ctx, s, ns, reinterpret_cast<const cx<double>*>(x));
+  });
+}
+
+int bem_warm_clear(bem_ctx* ctx) {
+  return guarded(ctx, [&] {
+    ctx->warm.s.clear();
+    ctx->warm.trained = false;
+    ctx->warm.r = 0;
+  });
+}
+
+int bem_warm_train(bem_ctx* ctx, const bem_warm_params* p, bem_warm_stats* st) {
+  return guarded(ctx, [&] {
+    BEM_REQUIRE(p, "null parameters");
+    BEM_REQUIRE(p->r_max >= 1 && p->r_max <= 64 && p->steps >= 1 && p->lr > 0 && p->rel_tol >= 0,
+                "bad warm-start parameters");
+    warm_train(ctx, *p, st);
+  });
+}
+
+int bem_warm_basis(bem_ctx* ctx, double* phi, int32_t* r) {
+  return guarded(ctx, [&] {
+    BEM_REQUIRE(ctx->warm.trained, "no trained warm start");
+    if (r) *r = ctx->warm.r;
+    if (phi) copy_out(ctx, phi, ctx->warm.Phi.p, sizeof(cx<double>) * ctx->warm.r * ctx->warm.N);
+  });
+}
+
+int bem_mlp_eval(bem_ctx* ctx, int32_t r, const float* params, const float* U, int32_t B,
+                 const float* T, float* y, float* grads, double* loss) {
+  return guarded(ctx, [&] {
+    BEM_REQUIRE(params && U && y && r >= 1 && r <= 64 && B >= 1 && B <= 4096, "bad argument");
+    BEM_REQUIRE(!T || grads, "targets given without a gradient buffer");
+    mlp_eval(ctx, r, params, U, B, T, y, grads, loss);
+  });
+}
+
 int bem_residual(bem_ctx* ctx, const double* s, int64_t ns, const double* x, double* r, int mode) {
   return guarded(ctx, [&] {
     need_mesh(ctx);

@@ -208,6 +208,19 @@ struct ProfRec {
   int64_t work;  // frequencies covered by the launch
 };
 
+// Learned / nearest warm start: stored solutions, POD basis and MLP parameters.
+struct WarmStart {
+  int64_t N = 0;              // unknowns of the stored solutions
+  std::vector<double> s;      // 2J: frequencies of the stored solutions
+  DevBuf X;                   // cx<double>[J][N]
+  DevBuf Phi;                 // cx<double>[r][N] POD basis
+  int r = 0;
+  DevBuf params;              // float MLP parameters (W1, b1, W2, b2, W3, b3)
+  DevBuf act;                 // activations scratch
+  double omega = 1, scale = 1;
+  bool trained = false;
+};
+
 }  // namespace bem
 
 struct bem_ctx {
@@ -220,6 +233,7 @@ struct bem_ctx {
   bem::Material mat;
   bem::BC bc;
   bem::FreqSet fs;
+  bem::WarmStart warm;
   // scratch buffers for vectors (grow-only)
   bem::DevBuf io_a, io_b;       // staging for ABI copies
   bem::DevBuf io_c, io_d, io_e; // staging for the FSM calls (samples, times, output, dofs)
@@ -314,6 +328,14 @@ int guarded_call(bem_ctx* ctx, Fn&& fn) {
   }
 }
 void need_problem(bem_ctx* ctx);  // mesh, material and boundary conditions set
+
+// mlp.cu
+void warm_store(bem_ctx* ctx, const double* s, int64_t ns, const cx<double>* x_dev);
+void warm_train(bem_ctx* ctx, const bem_warm_params& prm, bem_warm_stats* out);
+void warm_initial(bem_ctx* ctx, int mode, cx<double>* x0);
+void mlp_eval(bem_ctx* ctx, int r, const float* params_h, const float* U_h, int B, const float* T_h,
+              float* Y_h, float* grads_h, double* loss_h);
+int64_t mlp_n_params(int r);
 
 // helpers
 inline int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }

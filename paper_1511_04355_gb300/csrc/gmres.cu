@@ -238,11 +238,24 @@ __global__ void add_correction_kernel(cx<double>* x, const cx<T>* d, int64_t N, 
   x[t] = x[t] + widen(d[t]);
 }
 
+// r -= widen(y) for the instances flagged in mask
+__global__ void sub_widen_masked_kernel(cx<double>* r, const cx<float>* y, const int32_t* mask, int64_t N,
+                                        int64_t n) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n && mask[t / N]) r[t] = r[t] - widen(y[t]);
+}
+
+// r -= widen(y) for every entry
+__global__ void sub_widen_kernel(cx<double>* r, const cx<float>* y, int64_t n) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) r[t] = r[t] - widen(y[t]);
+}
+
 // r = b - Ax  (for active instances)
 __global__ void residual_kernel(const cx<double>* b, const cx<double>* Ax, cx<double>* r,
                                 int64_t N, int64_t F, const int32_t* act) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= F * N || !act[t / N]) return;
+  if (t >= F * N || (act && !act[t / N])) return;
   r[t] = b[t] - Ax[t];
 }
 
@@ -255,7 +268,7 @@ struct Work {
   DevBuf V, z, w, u;          // T
   DevBuf H, cs, sn, g, hacc, dots, y;
   DevBuf hnorm2, target, inv_h, est, bn2, rn2;
-  DevBuf act, part, kcols, status, nact;
+  DevBuf act, part, kcols, status, nact, upd;
 };
 
 template <class T>
@@ -403,7 +416,7 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
   W.dots.reserve(sizeof(cx<double>) * F * m1);
   W.y.reserve(sizeof(cx<double>) * F * m1);
   for (DevBuf* b : {&W.hnorm2, &W.target, &W.inv_h, &W.est, &W.bn2, &W.rn2}) b->reserve(sizeof(double) * F);
-  for (DevBuf* b : {&W.act, &W.part, &W.kcols, &W.status}) b->reserve(sizeof(int32_t) * F);
+  for (DevBuf* b : {&W.act, &W.part, &W.kcols, &W.status, &W.upd}) b->reserve(sizeof(int32_t) * F);
   W.nact.reserve(sizeof(int32_t));
   BEM_CUDA(cudaMemsetAsync(W.status.p, 0, sizeof(int32_t) * F, st));
 
@@ -427,19 +440,42 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
     ctx->launches++;
     BEM_CUDA(cudaMemcpyAsync(W.r.p, W.b.p, sizeof(cx<double>) * F * N, cudaMemcpyDeviceToDevice, st));
   }
-  // x = 0, r = b
-  BEM_CUDA(cudaMemsetAsync(x_dev, 0, sizeof(cx<double>) * F * N, st));
-  BEM_CUDA(cudaMemcpyAsync(W.rn2.p, W.bn2.p, sizeof(double) * F, cudaMemcpyDeviceToDevice, st));
+  const bool warm = o.warm_start != BEM_WARM_ZERO && ctx->warm.N == N && !ctx->warm.s.empty();
+  if (warm) {
+    // x0 from the warm start; r = b - A x0 with the operator of the inner solve's precision
+    warm_initial(ctx, o.warm_start, x_dev);
+    if (mixed) {
+      DevBuf xf, yf;
+      xf.reserve(sizeof(cx<float>) * F * N);
+      yf.reserve(sizeof(cx<float>) * F * N);
+      narrow_array(ctx, x_dev, xf.as<cx<float>>(), F * N);
+      apply_operator32(ctx, xf.as<cx<float>>(), yf.as<cx<float>>(), BEM_APPLY_A, nullptr);
+      sub_widen_kernel<<<grid_for(F * N, 256), 256, 0, st>>>(W.r.as<cx<double>>(), yf.as<cx<float>>(), F * N);
+    } else {
+      apply_operator64(ctx, x_dev, W.Ax.as<cx<double>>(), BEM_APPLY_A, nullptr);
+      residual_kernel<<<grid_for(F * N, 256), 256, 0, st>>>(W.b.as<cx<double>>(), W.Ax.as<cx<double>>(),
+                                                            W.r.as<cx<double>>(), N, F, nullptr);
+    }
+    ctx->launches++;
+    BEM_LAUNCHED();
+    norm2_kernel<double><<<(unsigned)F, 256, 0, st>>>(W.r.as<cx<double>>(), N, nullptr, W.rn2.as<double>());
+    ctx->launches++;
+  } else {
+    // x = 0, r = b
+    BEM_CUDA(cudaMemsetAsync(x_dev, 0, sizeof(cx<double>) * F * N, st));
+    BEM_CUDA(cudaMemcpyAsync(W.rn2.p, W.bn2.p, sizeof(double) * F, cudaMemcpyDeviceToDevice, st));
+  }
   std::vector<double> bn2(F), rn2(F), est(F), tgt(F);
   std::vector<int32_t> part(F, 1), stat(F);
   BEM_CUDA(cudaMemcpyAsync(bn2.data(), W.bn2.p, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
+  BEM_CUDA(cudaMemcpyAsync(rn2.data(), W.rn2.p, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
   BEM_CUDA(cudaStreamSynchronize(st));
-  rn2 = bn2;
   iters.assign(F, 0);
   refines.assign(F, 0);
   resid.assign(F, 1.0);
   status.assign(F, BEM_ERR_NOT_CONVERGED);
   std::vector<char> done(F, 0);
+  std::vector<char> full_done(F, 0);  // the full residual has been formed once
   for (int64_t f = 0; f < F; ++f)
     if (bn2[f] == 0.0) {  // zero right-hand side: x = 0 is exact
       done[f] = 1;
@@ -492,14 +528,41 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
       }
       if (!need_restart) break;
     }
-    // FP64 residual r = b - A x for the instances still working
+    // FP64-class residual r = b - A x for the instances still working
     BEM_CUDA(cudaMemcpyAsync(W.part.p, part.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
-    std::vector<int32_t> rlist;
+    {
+      std::vector<int32_t> upd(F);
+      for (int64_t f = 0; f < F; ++f) upd[f] = (part[f] && full_done[f]) ? 1 : 0;
+      BEM_CUDA(cudaMemcpyAsync(W.upd.p, upd.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
+    }
+    std::vector<int32_t> rlist, ulist, flist;
     for (int64_t f = 0; f < F; ++f)
-      if (part[f]) rlist.push_back((int32_t)f);
+      if (part[f]) {
+        rlist.push_back((int32_t)f);
+        (full_done[f] ? ulist : flist).push_back((int32_t)f);
+      }
     if (rlist.empty()) break;
-    if (mixed && o.residual_mode == BEM_RESID_DF64) residual_df(ctx, x_dev, W.r.as<cx<double>>(), &rlist);
-    else residual64(ctx, x_dev, W.r.as<cx<double>>(), &rlist);
+    // First refinement step of a frequency: the full FP64-class residual r = b - A x.  Later
+    // steps update it, r <- r - A d, with the correction d of the inner solve applied in the
+    // inner solve's precision: d is small (|d| ~ kappa |r| / |A|), so the product's rounding,
+    // ~eps_32 |A| |d|, stays ~1e-10 |b| below the tolerance being certified.
+    if (!flist.empty()) {
+      if (mixed && o.residual_mode == BEM_RESID_DF64) residual_df(ctx, x_dev, W.r.as<cx<double>>(), &flist);
+      else residual64(ctx, x_dev, W.r.as<cx<double>>(), &flist);
+    }
+    if (!ulist.empty()) {
+      if (mixed) {
+        apply_operator32(ctx, W.z.as<cx<float>>(), W.w.as<cx<float>>(), BEM_APPLY_A, &ulist);
+        sub_widen_masked_kernel<<<grid_for(F * N, 256), 256, 0, st>>>(W.r.as<cx<double>>(), W.w.as<cx<float>>(),
+                                                                       W.upd.as<int32_t>(), N, F * N);
+      } else {
+        apply_operator64(ctx, W.z.as<cx<double>>(), W.Ax.as<cx<double>>(), BEM_APPLY_A, &ulist);
+        residual_kernel<<<grid_for(F * N, 256), 256, 0, st>>>(W.r.as<cx<double>>(), W.Ax.as<cx<double>>(),
+                                                              W.r.as<cx<double>>(), N, F, W.upd.as<int32_t>());
+      }
+      ctx->launches++;
+    }
+    for (int32_t f : flist) full_done[f] = 1;
     norm2_kernel<double><<<(unsigned)F, 256, 0, st>>>(W.r.as<cx<double>>(), N, W.part.as<int32_t>(),
                                                       W.rn2.as<double>());
     ctx->launches += 1;

@@ -53,8 +53,11 @@ __device__ __forceinline__ cdf cfma_df(cdf a, cdf v, cdf o) { return cadd(o, cmu
 __global__ void __launch_bounds__(kTB) resid_df_kernel(const ResDfArgs a) {
   constexpr int TB = kTB, S = kS, FT = kFT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* acc = reinterpret_cast<double*>(smem_raw);                     // [6 FT][TB]
-  float* sq = reinterpret_cast<float*>(acc + 6 * FT * TB);               // [S][4][8]
+  // float-float accumulators [FT][3 components][4 floats (re.h, re.l, im.h, im.l)][TB]: the
+  // frequency loop stays rolled (the float-float body is large; unrolling it overflowed the
+  // instruction cache), so its sums live in shared memory rather than in registers
+  float* pacc = reinterpret_cast<float*>(smem_raw);                     // [FT * 12][TB]
+  float* sq = pacc + FT * 12 * TB;                                       // [S][4][8]
   float* sn = sq + S * 4 * 8;                                            // [S][8]
   cdf* sv = reinterpret_cast<cdf*>(sn + S * 8);                          // [S][FT][7]
   FreqDf* sfc = reinterpret_cast<FreqDf*>(sv + S * FT * 7);              // [FT]
@@ -76,8 +79,7 @@ __global__ void __launch_bounds__(kTB) resid_df_kernel(const ResDfArgs a) {
   }
   if (tid < FT) sfc[tid] = a.fc[a.flist[g0 + min(tid, nf - 1)]];
   if (tid == 0) *sC = a.C;
-#pragma unroll
-  for (int k = 0; k < 6 * FT; ++k) acc[k * TB + tid] = 0.0;
+  for (int k = 0; k < FT * 12; ++k) pacc[k * TB + tid] = 0.f;
   __syncthreads();
   // the amplitude e^{-Re(z)} depends on Re(s) only: shared by the group when Re(s) agrees
   bool same_re = true;
@@ -134,12 +136,6 @@ __global__ void __launch_bounds__(kTB) resid_df_kernel(const ResDfArgs a) {
     __syncthreads();
     const DfConst& C = *sC;
 
-    cdf part[FT][3];
-#pragma unroll
-    for (int k = 0; k < FT; ++k)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) part[k][c] = cmk(dfm(0.f, 0.f), dfm(0.f, 0.f));
-
     for (int e = 0; e < ns; ++e) {
       const bool self = (e0 + e == i);
       const float* nn = sn + 8 * e;
@@ -168,9 +164,8 @@ __global__ void __launch_bounds__(kTB) resid_df_kernel(const ResDfArgs a) {
           amp_s = df_exp_neg(mul(sfc[0].a_re, r), C);
           amp_p = df_exp_neg(mul(sfc[0].b_re, r), C);
         }
-#pragma unroll
-        for (int k = 0; k < FT; ++k) {
-          if (k >= nf) continue;
+#pragma unroll 1
+        for (int k = 0; k < nf; ++k) {
           const FreqDf& F = sfc[k];
           const cdf* v = sv + 7 * (e * FT + k);
           const df zr_s = mul(F.a_re, r), zr_p = mul(F.b_re, r);
@@ -189,7 +184,7 @@ __global__ void __launch_bounds__(kTB) resid_df_kernel(const ResDfArgs a) {
           cdf J;
           if (zr_s.h * zr_s.h + ph_s.h * ph_s.h < kZSeriesDf2) {
             J = cmk(m.d[kSeriesDf - 1], dfm(0.f, 0.f));
-#pragma unroll
+#pragma unroll 1
             for (int t = kSeriesDf - 2; t >= 0; --t) J = cadd(cmul(J, zs), cmk(m.d[t], dfm(0.f, 0.f)));
           } else {
             J = cscale(inv_r2, cmul(csub(gp, gs), F.inv_a2));
@@ -209,33 +204,38 @@ __global__ void __launch_bounds__(kTB) resid_df_kernel(const ResDfArgs a) {
           const cdf ru = cadd(cadd(cscale(rx, v[4]), cscale(ry, v[5])), cscale(rz, v[6]));
           const cdf crv = cmul(cscale(cu, csub(Pp, cscalef(3.f, J))), ru);
           const cdf t3p = csub(t3, crv);
-          part[k][0] = cadd(cadd(cfma_df(t1, v[0], part[k][0]), cmul(psi, v[4])),
-                            cadd(cscale(n0, t2), cscale(rx, t3p)));
-          part[k][1] = cadd(cadd(cfma_df(t1, v[1], part[k][1]), cmul(psi, v[5])),
-                            cadd(cscale(n1, t2), cscale(ry, t3p)));
-          part[k][2] = cadd(cadd(cfma_df(t1, v[2], part[k][2]), cmul(psi, v[6])),
-                            cadd(cscale(n2, t2), cscale(rz, t3p)));
+          const cdf o0 = cadd(cadd(cmul(t1, v[0]), cmul(psi, v[4])), cadd(cscale(n0, t2), cscale(rx, t3p)));
+          const cdf o1 = cadd(cadd(cmul(t1, v[1]), cmul(psi, v[5])), cadd(cscale(n1, t2), cscale(ry, t3p)));
+          const cdf o2 = cadd(cadd(cmul(t1, v[2]), cmul(psi, v[6])), cadd(cscale(n2, t2), cscale(rz, t3p)));
+          float* pa = pacc + (k * 12) * TB + tid;
+          const cdf oc[3] = {o0, o1, o2};
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float* pc = pa + (4 * c) * TB;
+            const df re = add(dfm(pc[0], pc[TB]), oc[c].r);
+            const df im = add(dfm(pc[2 * TB], pc[3 * TB]), oc[c].i);
+            pc[0] = re.h;
+            pc[TB] = re.l;
+            pc[2 * TB] = im.h;
+            pc[3 * TB] = im.l;
+          }
         }
       }
     }
-#pragma unroll
-    for (int k = 0; k < FT; ++k)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        acc[(6 * k + 2 * c) * TB + tid] += df_to(part[k][c].r);
-        acc[(6 * k + 2 * c + 1) * TB + tid] += df_to(part[k][c].i);
-      }
   }
   if (!valid) return;
   for (int k = 0; k < nf; ++k) {
     double* yo = a.yacc + ((int64_t)a.flist[g0 + k] * a.ne + i) * 6;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) atomicAdd(yo + c, acc[(6 * k + c) * TB + tid]);
+    for (int c = 0; c < 6; ++c) {
+      const float* pc = pacc + (k * 12 + 2 * c) * TB + tid;
+      atomicAdd(yo + c, (double)pc[0] + (double)pc[TB]);
+    }
   }
 }
 
 size_t resid_df_smem() {
-  return sizeof(double) * 6 * kFT * kTB + sizeof(float) * kS * 4 * 8 + sizeof(float) * kS * 8 +
+  return sizeof(float) * 12 * kFT * kTB + sizeof(float) * kS * 4 * 8 + sizeof(float) * kS * 8 +
          sizeof(cdf) * kS * kFT * 7 + sizeof(FreqDf) * kFT + sizeof(DfConst);
 }
 
@@ -285,7 +285,6 @@ void residual_df(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::ve
   const int64_t tb = grid_for(a.ne, kTB), groups = grid_for(nfl, kFT);
   const int64_t want = 4 * 152 * 2;
   int64_t nsplit = std::max<int64_t>(1, (want + tb * groups - 1) / (tb * groups));
-  nsplit = std::max<int64_t>(nsplit, (a.ne + 16 * kS - 1) / (16 * kS));
   nsplit = std::min<int64_t>(nsplit, 65535);
   int64_t chunk = (a.ne + nsplit - 1) / nsplit;
   chunk = ((chunk + kS - 1) / kS) * kS;
