@@ -5,15 +5,20 @@ from solutions the method has already computed (the adaptive sampling of Sec. 3 
 frequency at a time).  Definitions written out plainly:
 
 * POD: the r leading left singular vectors Phi (N x r) of the snapshot matrix X = [x(s_1) ..
-  x(s_J)] (library SVD), r = the number of singular values above rel_tol * sigma_1 (at most
-  r_max); coefficients c_j = Phi^H x(s_j).
+  x(s_J)] (library SVD); r is the smallest rank whose discarded energy sum_{k>r} sigma_k^2 is at
+  most energy_tol * sum_k sigma_k^2 (at most r_max); coefficients c_j = Phi^H x(s_j).
+* Targets: the network predicts only the direction of the coefficient vector: c_j / |c_j| turned
+  by the phase that makes its first (leading-mode) entry real and non-negative, as
+  [Re, Im] pairs.  Magnitude and phase are fixed at solve time (below).
 * MLP: u = (Re s / Omega, Im s / Omega) -> h1 = g(W1 u + b1) -> h2 = g(W2 h1 + b2)
   -> y = W3 h2 + b3 (y = [Re c, Im c] / scale), widths 2 -> 128 -> 128 -> 2r, with the tanh form
   of GELU, g(x) = x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))) (Hendrycks and Gimpel).
 * Loss: L = (1 / (2 B)) sum_batch |y - y_target|^2; gradients by the chain rule.
 * Adam (Kingma and Ba): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
   w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
-* Warm start: x0(s) = Phi c(s), c from the network output.
+* Warm start: the direction x^(s) = Phi c(s), c from the network output (or the stored solution
+  at the nearest stored frequency), scaled by the complex alpha that minimises |b - alpha A x^|:
+  alpha = (A x^)^H b / |A x^|^2 (a one-dimensional least-squares problem), x0 = alpha x^.
 """
 from __future__ import annotations
 
@@ -24,11 +29,13 @@ import numpy as np
 GELU_C = math.sqrt(2.0 / math.pi)
 
 
-def pod(X, r_max=32, rel_tol=1e-10):
+def pod(X, r_max=32, energy_tol=1e-10):
     """X: (N, J) complex snapshots -> Phi (N, r)."""
     U, S, _ = np.linalg.svd(X, full_matrices=False)
-    r = int(min(r_max, np.sum(S > rel_tol * S[0])))
-    return U[:, :r]
+    e = S ** 2
+    tail = np.concatenate([np.cumsum(e[::-1])[::-1][1:], [0.0]])   # sum_{k > r} sigma_k^2
+    r = int(np.argmax(tail <= energy_tol * e.sum())) + 1
+    return U[:, :min(r, r_max)]
 
 
 def gelu(x):
@@ -105,14 +112,25 @@ def features(s, omega):
     return np.stack([s.real / omega, s.imag / omega], axis=1)
 
 
-def targets(Phi, X, scale):
-    """[Re c, Im c] / scale with c = Phi^H x for each snapshot column of X."""
+def targets(Phi, X):
+    """[Re c~, Im c~] per snapshot column of X, c~ = c / |c| * conj(c_1) / |c_1|, c = Phi^H x."""
     C = Phi.conj().T @ X                     # (r, J)
-    return np.concatenate([C.real, C.imag], axis=0).T / scale
+    nrm = np.linalg.norm(C, axis=0)
+    nrm = np.where(nrm > 0, nrm, 1.0)
+    ph = np.where(np.abs(C[0]) > 0, np.conj(C[0]) / np.where(np.abs(C[0]) > 0, np.abs(C[0]), 1.0), 1.0)
+    C = C / nrm * ph
+    return np.concatenate([C.real, C.imag], axis=0).T
 
 
-def warm_start(p, Phi, s, omega, scale):
+def direction(p, Phi, s, omega):
+    """Predicted warm-start directions Phi c(s), (len(s), N)."""
     y, _ = forward(p, features(s, omega))
     r = Phi.shape[1]
-    C = (y[:, :r] + 1j * y[:, r:]) * scale
-    return C @ Phi.T                          # (len(s), N)
+    return (y[:, :r] + 1j * y[:, r:]) @ Phi.T
+
+
+def min_residual_scale(A, b, xh):
+    """x0 = alpha xh with alpha = (A xh)^H b / |A xh|^2 (alpha = 0 when A xh = 0)."""
+    y = A @ xh
+    d = np.vdot(y, y).real
+    return (np.vdot(y, b) / d if d > 0 else 0.0) * xh

@@ -182,3 +182,85 @@ def uneven_instances(n_inst: int = 16, seed: int = SEED, levels=(2, 3, 4, 5)):
         v, f = ellipsoid(lvl, axes)
         out.append((v, f, mat))
     return out
+
+
+# ----------------------------------------------------------------------------------------------
+# porous block
+# ----------------------------------------------------------------------------------------------
+def box_surface(L=(1.0, 1.0, 1.0), n=(8, 8, 8)):
+    """Surface of the box [0,Lx]x[0,Ly]x[0,Lz], each face split into squares of the grid n and
+    each square into two triangles; normals point out of the box (out of the solid).
+    Returns (verts, tris, face_id) with face_id in {0: x=0, 1: x=Lx, 2: y=0, 3: y=Ly, 4: z=0,
+    5: z=Lz}."""
+    L = np.asarray(L, dtype=np.float64)
+    verts, tris, fid = [], [], []
+    index = {}
+
+    def vid(p):
+        key = tuple(np.round(p, 12))
+        if key not in index:
+            index[key] = len(verts)
+            verts.append(p)
+        return index[key]
+
+    for axis in range(3):
+        a1, a2 = [d for d in range(3) if d != axis]
+        for side in (0, 1):
+            for i in range(n[a1]):
+                for j in range(n[a2]):
+                    corner = []
+                    for di, dj in ((0, 0), (1, 0), (1, 1), (0, 1)):
+                        p = np.zeros(3)
+                        p[axis] = side * L[axis]
+                        p[a1] = (i + di) * L[a1] / n[a1]
+                        p[a2] = (j + dj) * L[a2] / n[a2]
+                        corner.append(vid(p))
+                    for t in ((corner[0], corner[1], corner[2]), (corner[0], corner[2], corner[3])):
+                        tris.append(t)
+                        fid.append(2 * axis + side)
+    verts = np.array(verts)
+    tris = np.array(tris, dtype=np.int64)
+    # orient outward: the normal must point away from the box centre
+    p0, p1, p2 = verts[tris[:, 0]], verts[tris[:, 1]], verts[tris[:, 2]]
+    nrm = np.cross(p1 - p0, p2 - p0)
+    flip = np.einsum("ij,ij->i", nrm, (p0 + p1 + p2) / 3 - L / 2) < 0
+    tris[flip] = tris[flip][:, [0, 2, 1]]
+    return verts, tris.astype(np.int32), np.array(fid, dtype=np.int32)
+
+
+def porous_block(L=(1.0, 1.0, 1.0), n=(8, 8, 8), n_voids=27, radii=(0.08, 0.15), void_level=2,
+                 clearance=0.02, seed=SEED, p0=CAVITY_P0, material=CAVITY_MATERIAL):
+    """Block with seeded non-overlapping spherical voids (the porous-solid workloads): step
+    traction p0 (compressive, along +z into the block) on the face z = 0, the face z = Lz fixed,
+    every other face and every void traction-free.  Returns a CavityProblem-like record."""
+    rng = np.random.default_rng(seed)
+    L = np.asarray(L, dtype=np.float64)
+    bv, bt, fid = box_surface(L, n)
+    centres, rad = [], []
+    tries = 0
+    while len(centres) < n_voids and tries < 100000:
+        tries += 1
+        r = rng.uniform(*radii)
+        c = rng.uniform(r + clearance, L - r - clearance)
+        if all(np.linalg.norm(c - c2) > r + r2 + clearance for c2, r2 in zip(centres, rad)):
+            centres.append(c)
+            rad.append(r)
+    verts = [bv]
+    tris = [bt]
+    off = len(bv)
+    for c, r in zip(centres, rad):
+        v, f = icosphere(void_level, r, c, inward=True)
+        verts.append(v)
+        tris.append(f + off)
+        off += len(v)
+    verts = np.vstack(verts)
+    tris = np.vstack(tris).astype(np.int32)
+    ne = len(tris)
+    face = np.full(ne, -1, dtype=np.int32)
+    face[:len(bt)] = fid
+    bc_type = np.zeros(ne, dtype=np.int8)
+    bc_value = np.zeros((ne, 3))
+    bc_value[face == 4, 2] = p0            # traction +p0 e_z on z = 0 (pushes into the block)
+    bc_type[face == 5] = 1                 # z = Lz fixed (zero displacement)
+    return dict(verts=verts, tris=tris, face=face, material=material, bc_type=bc_type,
+                bc_value=bc_value, centres=np.array(centres), radii=np.array(rad))
