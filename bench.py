@@ -50,8 +50,11 @@ METRIC = "BEM frequency solves/s at 1e-6 rel. residual vs plain FP64 GPU; % FP32
 FLOPS_PER_UNIT_T = 159
 FLOPS_PER_UNIT_U = 113   # displacement-kernel (U) columns: the right-hand side pass
 FLOPS_PER_UNIT_RES = 221  # fused FP64 residual r = K k - A x: T and U per kernel evaluation
+# The same residual in float-float on the FP32 pipes (resid_df_kernel): FP32 flops per kernel
+# evaluation, FADD + FMUL + 2 FFMA thread-instructions of one launch (ncu executed-instruction
+# counters, 16 frequencies on 5120 triangles) divided by its units
+FLOPS_PER_UNIT_RES_DF = 2476
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FP64_NOMINAL_TFLOPS = 1.25
 
 
 def workload_config(n_gpus):
@@ -335,18 +338,20 @@ def run_gpu(args):
     units32 = fl32 * (ne * ne - ne) * 4
     peak32 = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     ach32 = units32 * FLOPS_PER_UNIT_T / (ms32 / 1e3) / 1e12 if ms32 > 0 else 0.0
-    # FP64 refinement residual (fused U + T far-field sweep), one launch per refinement step
+    # FP64-class refinement residual (fused U + T far-field sweep in float-float on the FP32
+    # pipes), one launch per full residual
     n64, ms64, fl64 = per_step["res64"]
-    flops64 = fl64 * (ne * ne - ne) * 4 * FLOPS_PER_UNIT_RES
+    flops64 = fl64 * (ne * ne - ne) * 4 * FLOPS_PER_UNIT_RES_DF
     ach64 = flops64 / (ms64 / 1e3) / 1e12 if ms64 > 0 else 0.0
     roof32 = {"kernel": "far_kernel<float> (FP32 far-field operator)", "bound": "alu",
               "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
               "traffic": None, "launches_per_step": n32, "ms_per_step": ms32,
               "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (recipe unit counts, max clock)"}
-    roof64 = {"kernel": "far_kernel<double, resid> (FP64 refinement residual r = K k - A x)",
-              "bound": "alu", "achieved": ach64, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-              "frac": ach64 / FP64_NOMINAL_TFLOPS, "traffic": None, "launches_per_step": n64,
-              "ms_per_step": ms64, "peak_note": "nominal GB300 FP64 1.25 TFLOP/s (recipe table)"}
+    roof64 = {"kernel": "resid_df_kernel (FP64-class refinement residual r = K k - A x, float-float)",
+              "bound": "alu", "achieved": ach64, "peak": peak32, "unit": "TFLOP/s",
+              "frac": ach64 / peak32, "traffic": None, "launches_per_step": n64,
+              "ms_per_step": ms64, "flop_per_unit": FLOPS_PER_UNIT_RES_DF,
+              "peak_note": "FP32 pipes: 152 SMs x 128 lanes x 2 x 2070 MHz (recipe unit counts, max clock)"}
     roofline = roof64 if dominant == "res64" else roof32
 
     cpu_v, cpu_sample, _ = (None, None, None)
@@ -363,6 +368,7 @@ def run_gpu(args):
         "clocks": clocks,
         "roofline": roofline,
         "roofline_fp32_operator": roof32,
+        "roofline_residual": roof64,
         "kernel_ms_per_step": {k: v[1] for k, v in per_step.items()},
         "fp64_gpu_path": {"value": fp64_value, "unit": "solves/s",
                           "sample": f"{len(sel)} of the {N_FREQ} frequencies (every {N_FREQ // len(sel)}th)",
@@ -384,6 +390,31 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def kernel_case():
+    """Small case for ncu captures of the operator kernels: the 5120-triangle cavity, 16 of the
+    benchmark frequencies (every 8th), one FP32 operator application and one float-float
+    refinement residual, each after a warm-up call."""
+    import torch
+
+    import paper_1511_04355_gb300 as P
+
+    prob = W.spherical_cavity(level=LEVEL, n_freq=N_FREQ, T=T_WIN, sigma=SIGMA)
+    c = P.Context(0)
+    c.set_mesh(prob.verts, prob.tris)
+    m = prob.material
+    c.set_material(m.mu, m.nu, m.rho)
+    c.set_bc(prob.bc_type, prob.bc_value)
+    ne = len(prob.tris)
+    s = prob.s[::8]
+    x = torch.from_numpy(W.random_complex_vectors(len(s), 3 * ne) * 1e-6).cuda()
+    y = torch.zeros_like(x)
+    for _ in range(2):
+        P.bem_apply(c.h, s, x, y, P.BEM_PREC_FP32, P.BEM_APPLY_A)
+        P.bem_residual(c.h, s, x, y, P.BEM_RESID_DF64)
+    torch.cuda.synchronize()
+    print("kernel case done")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,7 +422,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--kernel-case", action="store_true",
+                    help="run only the small operator/residual case used for ncu captures")
     args = ap.parse_args()
+    if args.kernel_case:
+        kernel_case()
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

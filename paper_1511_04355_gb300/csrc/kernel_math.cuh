@@ -56,6 +56,16 @@ __device__ __forceinline__ cx<float> exp_neg_ff(float re, float ph_hi, float ph_
   return mk(amp * cs, -amp * sn);
 }
 
+// the same with the amplitude e^{-re} supplied (shared by frequencies with equal Re s)
+__device__ __forceinline__ cx<float> cis_neg_ff(float amp, float ph_hi, float ph_lo) {
+  const float k = rintf(ph_hi * 0.159154943091895336f);
+  float red = fmaf(-k, 6.28318548202514648f, ph_hi);
+  red = fmaf(-k, -1.74845560007440834e-07f, red) + ph_lo;
+  float sn, cs;
+  __sincosf(red, &sn, &cs);
+  return mk(amp * cs, -amp * sn);
+}
+
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 
@@ -93,15 +103,29 @@ __device__ __forceinline__ void phase_exps(cx<double> zs, cx<double> zp, double,
   Ep = exp_neg(zp);
 }
 
-// r_lo: low part of the distance (float-float distance in the FP32 kernels, 0 otherwise)
+// r_lo: low part of the distance (float-float distance in the FP32 kernels, 0 otherwise);
+// amp_s/amp_p > 0: precomputed amplitudes e^{-Re z} (FP32 kernels, common Re s)
 template <class R>
 __device__ __forceinline__ Radial<R> radial(R r, R inv_r2, const FreqC<R>& fc, const MatC<R>& m,
-                                            R r_lo = R(0)) {
+                                            R r_lo = R(0), float amp_s = -1.f, float amp_p = -1.f) {
   Radial<R> o;
   const cx<R> zs = r * fc.a;
   const cx<R> zp = m.beta * zs;
   cx<R> Ep;
-  phase_exps(zs, zp, r, r_lo, fc, o.Es, Ep);
+  if constexpr (sizeof(R) == 4) {
+    if (amp_s >= 0.f) {
+      const float ps = fc.ai_hi * r;
+      const float ps_lo = fmaf(fc.ai_hi, r, -ps) + fmaf(fc.ai_hi, r_lo, fc.ai_lo * r);
+      const float pp = fc.bi_hi * r;
+      const float pp_lo = fmaf(fc.bi_hi, r, -pp) + fmaf(fc.bi_hi, r_lo, fc.bi_lo * r);
+      o.Es = cis_neg_ff(amp_s, ps, ps_lo);
+      Ep = cis_neg_ff(amp_p, pp, pp_lo);
+    } else {
+      phase_exps(zs, zp, r, r_lo, fc, o.Es, Ep);
+    }
+  } else {
+    phase_exps(zs, zp, r, r_lo, fc, o.Es, Ep);
+  }
   o.gs = cfma(zs, o.Es, o.Es);
   o.gp = cfma(zp, Ep, Ep);
   o.P = axpy(-m.beta2, Ep, o.Es);

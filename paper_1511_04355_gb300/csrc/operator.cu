@@ -177,6 +177,13 @@ __global__ void __launch_bounds__(TB) far_kernel(const FarArgs<R> a) {
 #pragma unroll
   for (int k = 0; k < 6 * FT; ++k) acc[k * TB + tid] = R(0);
   const MatC<R>& m = a.m;
+  __syncthreads();
+  // FP32: when the group's frequencies share Re s, the amplitudes e^{-Re(s) r / c} are formed
+  // once per source point instead of once per frequency
+  bool same_re = FF;
+  for (int k = 1; k < nf; ++k) same_re = same_re && (float)sfc[k].a.r == (float)sfc[0].a.r;
+  const float re_s = FF ? -(float)sfc[0].a.r : 0.f;
+  const float re_p = FF ? -(float)(sfc[0].a.r * m.beta) : 0.f;
   const R inv4pi = R(kInv4Pi);
 
   for (int64_t e0 = src0; e0 < src1; e0 += S) {
@@ -251,12 +258,17 @@ __global__ void __launch_bounds__(TB) far_kernel(const FarArgs<R> a) {
         const R drdn = rh0 * nn.x + rh1 * nn.y + rh2 * nn.z;
         const R cw = w * inv_r2 * inv4pi;
         const R cu = w * rinv * m.inv4pimu;
+        float amp_s = -1.f, amp_p = -1.f;
+        if (same_re) {
+          amp_s = __expf(re_s * (float)r);
+          amp_p = __expf(re_p * (float)r);
+        }
         if (RESID || !isU) {
 #pragma unroll
           for (int k = 0; k < FT; ++k) {
             if (!((mask >> k) & 1u)) continue;
             const cx<R>* v = sv + NV * (e * FT + k);
-            const Radial<R> K = radial(r, inv_r2, sfc[k], m, r_lo);
+            const Radial<R> K = radial(r, inv_r2, sfc[k], m, r_lo, amp_s, amp_p);
             const TCoef<R> T = tcoef(K, m);
             t_contract(T, cw, drdn, rh0, rh1, rh2, nn.x, nn.y, nn.z, v[0], v[1], v[2], v[3], part[k]);
             if (RESID) u_contract(K, cu, rh0, rh1, rh2, v[4], v[5], v[6], part[k]);
@@ -266,7 +278,7 @@ __global__ void __launch_bounds__(TB) far_kernel(const FarArgs<R> a) {
           for (int k = 0; k < FT; ++k) {
             if (!((mask >> k) & 1u)) continue;
             const cx<R>* v = sv + NV * (e * FT + k);
-            const Radial<R> K = radial(r, inv_r2, sfc[k], m, r_lo);
+            const Radial<R> K = radial(r, inv_r2, sfc[k], m, r_lo, amp_s, amp_p);
             u_contract(K, cu, rh0, rh1, rh2, v[0], v[1], v[2], part[k]);
           }
         }
@@ -464,8 +476,8 @@ struct Geo<double> {
 template <class R>
 struct Cfg;
 template <>
-struct Cfg<float> {  // FP32: 128 targets x 8 frequencies per CTA, 64-element source tiles
-  static constexpr int TB = 128, S = 64, FT = 8, kPerSM = 4;
+struct Cfg<float> {  // FP32: 128 targets x 8 frequencies per CTA, 32-element source tiles
+  static constexpr int TB = 128, S = 32, FT = 8, kPerSM = 5;
 };
 template <>
 struct Cfg<double> {  // FP64: 128 targets x 4 frequencies per CTA, 32-element source tiles
