@@ -202,8 +202,10 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.current_stream(dev)
 
+    from paper_1511_04355_gb300 import shard as SH
+
     prob = W.spherical_cavity(level=LEVEL, n_freq=N_FREQ * ws, T=T_WIN, sigma=SIGMA)
-    s_all = prob.s[rank * N_FREQ:(rank + 1) * N_FREQ]
+    s_all = SH.shard(prob.s, rank, ws)              # N_FREQ contiguous frequencies per rank
     ne = len(prob.tris)
     n_unk = 3 * ne
     m = prob.material
@@ -251,13 +253,8 @@ def run_gpu(args):
             infos.append(info)
     ktimes = ctx.kernel_times()
     ctx.profile(False)
-    t_step = float(np.mean(times))
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
-    value = ws * N_FREQ / (t_step / 1e3)
+    t_step = SH.max_over_ranks(float(np.mean(times)), dev)
+    value = SH.aggregate_rate(N_FREQ, ws, t_step / 1e3)
 
     # e2e through the ABI with host buffers (pinned), every step uploads mesh, data, s and
     # downloads all solutions
@@ -284,13 +281,8 @@ def run_gpu(args):
         e2e_step()
         barrier()
         et.append(time.perf_counter() - t0)
-    t_e2e = float(np.mean(et))
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-    e2e_value = ws * N_FREQ / t_e2e
+    t_e2e = SH.max_over_ranks(float(np.mean(et)), dev)
+    e2e_value = SH.aggregate_rate(N_FREQ, ws, t_e2e)
 
     # accuracy and the plain-FP64 GPU path on a sample of the band
     sel = np.arange(0, N_FREQ, N_FREQ // FP64_SAMPLE)
@@ -391,9 +383,10 @@ def run_gpu(args):
 
 
 def kernel_case():
-    """Small case for ncu captures of the operator kernels: the 5120-triangle cavity, 16 of the
-    benchmark frequencies (every 8th), one FP32 operator application and one float-float
-    refinement residual, each after a warm-up call."""
+    """Small case for ncu captures of the operator kernels: the 5120-triangle cavity, 16
+    consecutive benchmark frequencies (s_56 .. s_71, equally spaced: the FP32 operator runs them
+    through its recurrence kernel), one FP32 operator application and one float-float refinement
+    residual, each after a warm-up call."""
     import torch
 
     import paper_1511_04355_gb300 as P
@@ -405,7 +398,7 @@ def kernel_case():
     c.set_material(m.mu, m.nu, m.rho)
     c.set_bc(prob.bc_type, prob.bc_value)
     ne = len(prob.tris)
-    s = prob.s[::8]
+    s = prob.s[56:72]
     x = torch.from_numpy(W.random_complex_vectors(len(s), 3 * ne) * 1e-6).cuda()
     y = torch.zeros_like(x)
     for _ in range(2):

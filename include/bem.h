@@ -149,6 +149,29 @@ int bem_set_bc(bem_ctx* ctx, const int8_t* bc_type, const double* bc_value, int 
 int bem_solve_frequencies(bem_ctx* ctx, const double* s, int64_t ns, double* x_out,
                           bem_solve_stats* stats);
 
+/* Several independent problems in one call: item k solves its context's problem (mesh,
+ * material, boundary data and options, set beforehand) at its own ns frequencies s[ns]
+ * (complex), with x_out and stats as for bem_solve_frequencies.  The paper solves one problem
+ * at a time; batching uneven problems is this library's, to keep the GPU busy when the
+ * problems are small.  Up to max_workers host threads (0: one per item) each drive one
+ * context through bem_solve_frequencies on that context's own stream, largest problem
+ * (ne^2 x ns) first, so kernels of different problems run side by side on the GPU.  Every
+ * item needs a distinct context; contexts created with separate streams (the default) run
+ * concurrently, contexts sharing a caller stream run one after another.  Out: items[k].status =
+ * that solve's return code.  Returns BEM_OK when every item succeeded, else the first failing
+ * code (an error other than BEM_ERR_NOT_CONVERGED takes precedence); INVALID_ARG for a null or
+ * repeated context or an empty frequency list (nothing is run). */
+typedef struct bem_batch_item {
+  bem_ctx* ctx;
+  const double* s;         /* [ns] complex frequencies (host or device)                  */
+  int64_t ns;
+  double* x_out;           /* [ns x 3ne] complex (host or device), nullable               */
+  bem_solve_stats* stats;  /* nullable                                                     */
+  int32_t status;          /* out                                                          */
+} bem_batch_item;
+
+int bem_solve_batch(bem_batch_item* items, int32_t n, int32_t max_workers);
+
 /* ------------------------------------------------------------------ time domain (FSM) */
 
 /* Fourier-series-method inverse Laplace transform (step a9; Sec. 2.2, Eqs. (invLap),
@@ -198,15 +221,18 @@ const char* bem_noalloc_last_error(void);
 
 /* The warm start gives each new frequency solve an initial guess built from solutions already
  * computed (the paper's adaptive sampling solves one new frequency at a time next to solved
- * ones; the warm start itself is not in the paper).  BEM_WARM_NEAREST: the stored solution at
- * the nearest stored frequency.  BEM_WARM_MLP: x0(s) = Phi c(s), Phi = the leading left singular
- * vectors (POD) of the stored solutions, c(s) predicted by a 2 -> 128 -> 128 -> 2r MLP (tanh-GELU)
- * trained on the stored (s, Phi^H x) pairs; its dense layers run on the tensor cores (FP16
- * operands, FP32 accumulation), the rest in FP32.  The GMRES tolerance is unchanged, so the
- * warm start changes the iteration count, never the accepted accuracy. */
+ * ones; the warm start itself is not in the paper).  Both modes first pick a direction x^:
+ * BEM_WARM_NEAREST the stored solution at the nearest stored frequency; BEM_WARM_MLP
+ * x^ = Phi c(s), Phi = the leading left singular vectors (POD) of the stored solutions, c(s)
+ * predicted by a 2 -> 128 -> 128 -> 2r MLP (tanh-GELU) trained on the directions of the stored
+ * coefficient vectors Phi^H x (unit norm, leading entry real and non-negative); its dense layers
+ * run on the tensor cores (FP16 operands, FP32 accumulation), the rest in FP32.  The solve then
+ * scales the direction by the complex alpha minimising |b - alpha A x^| (one operator product,
+ * which also gives the initial residual), so |r0| <= |b|.  The GMRES tolerance is unchanged:
+ * the warm start changes the iteration count, never the accepted accuracy. */
 typedef struct bem_warm_params {
   int32_t r_max;    /* POD rank cap (32)                                               */
-  double rel_tol;   /* keep singular values > rel_tol * sigma_1 (1e-10)                */
+  double energy_tol; /* POD energy cut: drop modes holding <= energy_tol of sum sigma^2 (1e-10) */
   int32_t steps;    /* Adam steps (2000)                                               */
   double lr;        /* Adam learning rate (1e-3; beta1 0.9, beta2 0.999, eps 1e-8)      */
   uint64_t seed;    /* weight initialisation (uniform +-1/sqrt(fan_in), zero biases)    */
@@ -232,6 +258,11 @@ int bem_warm_clear(bem_ctx* ctx);
 int bem_warm_train(bem_ctx* ctx, const bem_warm_params* p, bem_warm_stats* stats);
 /* The trained POD basis: phi[r x 3ne] complex (host or device, NULL to query r). */
 int bem_warm_basis(bem_ctx* ctx, double* phi, int32_t* r);
+/* The warm-start direction x^(s) a solve would start from (before its minimal-residual scaling),
+ * for ns frequencies s[ns] (complex, host or device): x_out[ns x 3ne] complex (host or device).
+ * mode: BEM_WARM_NEAREST (needs stored solutions) or BEM_WARM_MLP (needs bem_warm_train).
+ * Errors: INVALID_ARG (other mode, nothing stored or trained, or stored for another mesh). */
+int bem_warm_predict(bem_ctx* ctx, int32_t mode, const double* s, int64_t ns, double* x_out);
 /* One MLP pass with caller parameters (verification): params (host, float, the layout
  * W1[128x2], b1[128], W2[128x128], b2[128], W3[2r x 128], b3[2r], row-major), inputs U[B x 2],
  * targets T[B x 2r] (nullable: forward only).  Outputs (host): y[B x 2r]; grads[nparams] and

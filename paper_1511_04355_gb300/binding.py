@@ -86,13 +86,18 @@ class bem_afs_stats(C.Structure):
 
 
 class bem_warm_params(C.Structure):
-    _fields_ = [("r_max", C.c_int32), ("rel_tol", C.c_double), ("steps", C.c_int32),
+    _fields_ = [("r_max", C.c_int32), ("energy_tol", C.c_double), ("steps", C.c_int32),
                 ("lr", C.c_double), ("seed", C.c_uint64), ("reserved", C.c_int32 * 4)]
 
 
 class bem_warm_stats(C.Structure):
     _fields_ = [("r", C.c_int32), ("n_snapshots", C.c_int32), ("loss_first", C.c_double),
                 ("loss_last", C.c_double), ("seconds", C.c_double)]
+
+
+class bem_batch_item(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("s", C.c_void_p), ("ns", C.c_int64), ("x_out", C.c_void_p),
+                ("stats", C.POINTER(bem_solve_stats)), ("status", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -120,6 +125,8 @@ _SIGS = {
     "bem_warm_clear": (C.c_int, [_P]),
     "bem_warm_train": (C.c_int, [_P, C.POINTER(bem_warm_params), C.POINTER(bem_warm_stats)]),
     "bem_warm_basis": (C.c_int, [_P, _P, C.POINTER(C.c_int32)]),
+    "bem_solve_batch": (C.c_int, [C.POINTER(bem_batch_item), C.c_int32, C.c_int32]),
+    "bem_warm_predict": (C.c_int, [_P, C.c_int32, _P, _I64, _P]),
     "bem_mlp_eval": (C.c_int, [_P, C.c_int32, _P, _P, C.c_int32, _P, _P, _P, C.POINTER(C.c_double)]),
     "bem_vf_fit": (C.c_int, [_P, _I64, _P, _I64, _P, C.c_int32, C.c_int32, C.c_double, C.c_int32, _P, _P]),
     "bem_vf_eval": (C.c_int, [_P, C.c_int32, _P, _I64, _P, _I64, _P]),
@@ -254,6 +261,46 @@ def bem_solve_frequencies(ctx, s, x_out=None, allow_not_converged=False):
                 fp64_operator_applies=stats.fp64_operator_applies,
                 kernel_launches=stats.kernel_launches, rc=rc)
     return x_out, info
+
+
+def bem_solve_batch(problems, max_workers=0, allow_not_converged=False):
+    """problems: list of (ctx handle, s, x_out) with x_out as in bem_solve_frequencies (None:
+    a new host array; the context's element count is then needed, so pass an array).  Returns
+    a list of (x_out, stats dict) in the order given."""
+    n = len(problems)
+    items = (bem_batch_item * n)()
+    keep = []
+    outs = []
+    for k, (ctx, s, x_out) in enumerate(problems):
+        s, ns = _cplx_as_pairs(s)
+        stats = bem_solve_stats()
+        arrs = dict(iterations=np.zeros(ns, np.int32), refinements=np.zeros(ns, np.int32),
+                    residual=np.zeros(ns, np.float64), status=np.zeros(ns, np.int32))
+        stats.iterations = arrs["iterations"].ctypes.data_as(C.POINTER(C.c_int32))
+        stats.refinements = arrs["refinements"].ctypes.data_as(C.POINTER(C.c_int32))
+        stats.residual = arrs["residual"].ctypes.data_as(C.POINTER(C.c_double))
+        stats.status = arrs["status"].ctypes.data_as(C.POINTER(C.c_int32))
+        keep += [s, stats, arrs]
+        items[k].ctx = ctx
+        items[k].s = _ptr(s)
+        items[k].ns = ns
+        items[k].x_out = _ptr(x_out)
+        items[k].stats = C.pointer(stats)
+        outs.append((x_out, stats, arrs))
+    rc = load_library().bem_solve_batch(items, n, max_workers)
+    if rc != BEM_OK and not (allow_not_converged and rc == BEM_ERR_NOT_CONVERGED):
+        bad = [k for k in range(n) if items[k].status != BEM_OK]
+        k = bad[0] if bad else 0
+        msg = load_library().bem_last_error(problems[k][0])
+        raise BemError(rc, f"bem_solve_batch: item {k} failed with {items[k].status}: "
+                           f"{msg.decode() if msg else ''}")
+    res = []
+    for k, (x_out, stats, arrs) in enumerate(outs):
+        info = dict(arrs, seconds=stats.seconds, fp32_operator_applies=stats.fp32_operator_applies,
+                    fp64_operator_applies=stats.fp64_operator_applies,
+                    kernel_launches=stats.kernel_launches, rc=items[k].status)
+        res.append((x_out, info))
+    return res
 
 
 def bem_geometry(ctx, ne):
@@ -481,6 +528,14 @@ def bem_warm_basis(ctx, n_unknowns):
     phi = np.zeros((r.value, n_unknowns), np.complex128)
     _check(ctx, load_library().bem_warm_basis(ctx, _ptr(phi), C.byref(r)), "bem_warm_basis")
     return phi
+
+
+def bem_warm_predict(ctx, mode, s, n_unknowns):
+    """Warm-start directions x^(s), (len(s), n_unknowns) complex, host."""
+    s, ns = _cplx_as_pairs(s)
+    x = np.zeros((ns, n_unknowns), np.complex128)
+    _check(ctx, load_library().bem_warm_predict(ctx, mode, _ptr(s), ns, _ptr(x)), "bem_warm_predict")
+    return x
 
 
 def bem_mlp_eval(ctx, r, params, U, T=None):

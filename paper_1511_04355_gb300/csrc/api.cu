@@ -1,6 +1,7 @@
 // extern "C" entry points of the library: argument checking, host/device marshalling and
 // orchestration of the kernels in geometry.cu, operator.cu and gmres.cu.  Every C++ exception
 // is turned into a BEM_ERR_* code plus a message (bem_last_error), so no error escapes the ABI.
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <mutex>
@@ -239,6 +240,14 @@ int bem_set_mesh(bem_ctx* ctx, const double* verts, int64_t nv, const int32_t* t
     m.verts.assign(verts, verts + 3 * nv);
     m.tris.assign(tris, tris + 3 * ne);
     m.ne = ne;
+    double lo[3] = {verts[0], verts[1], verts[2]}, hi[3] = {verts[0], verts[1], verts[2]};
+    for (int64_t k = 0; k < nv; ++k)
+      for (int c = 0; c < 3; ++c) {
+        lo[c] = std::min(lo[c], verts[3 * k + c]);
+        hi[c] = std::max(hi[c], verts[3 * k + c]);
+      }
+    m.diam = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                       (hi[2] - lo[2]) * (hi[2] - lo[2]));
     ctx->bc.set = false;
     ctx->fs.valid = false;
     try {
@@ -375,7 +384,7 @@ int bem_default_warm_params(bem_warm_params* p) {
   if (!p) return BEM_ERR_INVALID_ARG;
   std::memset(p, 0, sizeof *p);
   p->r_max = 32;
-  p->rel_tol = 1e-10;
+  p->energy_tol = 1e-10;
   p->steps = 2000;
   p->lr = 1e-3;
   p->seed = 20151113ull;
@@ -401,9 +410,23 @@ int bem_warm_clear(bem_ctx* ctx) {
 int bem_warm_train(bem_ctx* ctx, const bem_warm_params* p, bem_warm_stats* st) {
   return guarded(ctx, [&] {
     BEM_REQUIRE(p, "null parameters");
-    BEM_REQUIRE(p->r_max >= 1 && p->r_max <= 64 && p->steps >= 1 && p->lr > 0 && p->rel_tol >= 0,
+    BEM_REQUIRE(p->r_max >= 1 && p->r_max <= 64 && p->steps >= 1 && p->lr > 0 && p->energy_tol >= 0 && p->energy_tol < 1,
                 "bad warm-start parameters");
     warm_train(ctx, *p, st);
+  });
+}
+
+int bem_warm_predict(bem_ctx* ctx, int32_t mode, const double* s, int64_t ns, double* x_out) {
+  return guarded(ctx, [&] {
+    need_mesh(ctx);
+    BEM_REQUIRE(s && x_out && ns >= 1, "bad argument");
+    BEM_REQUIRE(mode == BEM_WARM_NEAREST || mode == BEM_WARM_MLP, "mode must be BEM_WARM_NEAREST or BEM_WARM_MLP");
+    std::vector<double> sh(2 * ns);
+    copy_out(ctx, sh.data(), s, sizeof(double) * 2 * ns);
+    const int64_t n = ns * 3 * ctx->mesh.ne;
+    ctx->io_a.reserve(sizeof(cx<double>) * n);
+    warm_initial(ctx, mode, sh.data(), ns, ctx->io_a.as<cx<double>>());
+    copy_out(ctx, x_out, ctx->io_a.p, sizeof(cx<double>) * n);
   });
 }
 

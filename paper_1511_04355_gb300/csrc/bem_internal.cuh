@@ -112,6 +112,14 @@ struct FreqC {
   R ai_hi, ai_lo, bi_hi, bi_lo;
 };
 
+// A far-kernel CTA's frequencies: entries [start, start + count) of the staged frequency list.
+// In an equally spaced group (recurrence kernel) s_j = s_0 + j i delta, and (ws, wp) are the
+// phase slopes of one step, delta / c_s and beta delta / c_s, as float-float pairs.
+struct FarGroup {
+  int32_t start, count;
+  float ws_hi, ws_lo, wp_hi, wp_lo;
+};
+
 // Four packed doubles (centroid + h, normal + area, quadrature point + weight).
 struct alignas(32) D4 {
   double x, y, z, w;
@@ -171,6 +179,7 @@ struct Mesh {
   DevBuf near_ptr, near_col;   // int32 CSR
   int64_t nnz = 0;
   std::vector<int32_t> h_near_ptr, h_near_col;
+  double diam = 0;             // bounding-box diagonal (bounds every source-target distance)
 };
 
 struct Material {
@@ -217,7 +226,7 @@ struct WarmStart {
   int r = 0;
   DevBuf params;              // float MLP parameters (W1, b1, W2, b2, W3, b3)
   DevBuf act;                 // activations scratch
-  double omega = 1, scale = 1;
+  double omega = 1;
   bool trained = false;
 };
 
@@ -241,6 +250,9 @@ struct bem_ctx {
   bem::DevBuf active;           // int32[F] per-frequency active flags
   bem::DevBuf flist_d;          // int32 frequency list of the current operator launch
   std::vector<int32_t> flist_h;
+  bem::DevBuf groups_d;         // FarGroup per CTA frequency group of the current far launches
+  std::vector<bem::FarGroup> groups_h;
+  int64_t rec_entries = 0;      // leading list entries in equally spaced runs (FP32 recurrence)
   bem::DevBuf yacc;             // FP64 far-field accumulator [F][ne][3] complex
   int64_t launches = 0;         // kernels launched (accumulated, reset per call)
   int64_t f32_applies = 0, f64_applies = 0;
@@ -279,7 +291,7 @@ void residual_df(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::ve
 void build_freq_df(bem_ctx* ctx, const double* s, int64_t F);
 // helpers shared by the far kernels: stage the frequency list + zero the FP64 accumulator, and
 // the FP64 near-field/own-element pass of the residual
-int64_t stage_flist(bem_ctx* ctx, const std::vector<int32_t>* flist);
+int64_t stage_flist(bem_ctx* ctx, const std::vector<int32_t>* flist, int rec_ft);
 void near_residual64(bem_ctx* ctx, const cx<double>* x, cx<double>* r, int64_t nfl);
 void apply_precond64(bem_ctx* ctx, const cx<double>* x, cx<double>* y, const int32_t* active);
 void apply_precond32(bem_ctx* ctx, const cx<float>* x, cx<float>* y, const int32_t* active);
@@ -332,7 +344,7 @@ void need_problem(bem_ctx* ctx);  // mesh, material and boundary conditions set
 // mlp.cu
 void warm_store(bem_ctx* ctx, const double* s, int64_t ns, const cx<double>* x_dev);
 void warm_train(bem_ctx* ctx, const bem_warm_params& prm, bem_warm_stats* out);
-void warm_initial(bem_ctx* ctx, int mode, cx<double>* x0);
+void warm_initial(bem_ctx* ctx, int mode, const double* s, int64_t F, cx<double>* x0);
 void mlp_eval(bem_ctx* ctx, int r, const float* params_h, const float* U_h, int B, const float* T_h,
               float* Y_h, float* grads_h, double* loss_h);
 int64_t mlp_n_params(int r);

@@ -50,25 +50,34 @@ __device__ __forceinline__ df two_sum2(float a, float b) {
   return dfm(s, (a - (s - bb)) + (b - bb));
 }
 __device__ __forceinline__ df neg(df a) { return dfm(-a.h, -a.l); }
+// Inside expressions the pairs are left unnormalised: the sum of the high parts is split exactly
+// (TwoSum) and the low parts are added, but no final Quick-Two-Sum renormalises the result
+// (|l| may then exceed ulp(h)/2 by a few ulps).  h + l still carries the value; a later product
+// loses at most ~u |l| |b| (u = 2^-24), which after a cancellation of ratio c is ~u^2/c relative,
+// the order of the error the cancellation itself leaves.  add_n renormalises, for running sums.
 __device__ __forceinline__ df add(df a, df b) {
   const df s = two_sum2(a.h, b.h);
-  return quick2(s.h, s.l + (a.l + b.l));
+  return dfm(s.h, s.l + (a.l + b.l));
+}
+__device__ __forceinline__ df add_n(df a, df b) {
+  const df s = two_sum2(a.h, b.h);
+  return two_sum2(s.h, s.l + (a.l + b.l));
 }
 __device__ __forceinline__ df sub(df a, df b) { return add(a, neg(b)); }
 __device__ __forceinline__ df addf(df a, float b) {
   const df s = two_sum2(a.h, b);
-  return quick2(s.h, s.l + a.l);
+  return dfm(s.h, s.l + a.l);
 }
 __device__ __forceinline__ df mul(df a, df b) {
   const float p = a.h * b.h;
   float e = fmaf(a.h, b.h, -p);
   e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
-  return quick2(p, e);
+  return dfm(p, e);
 }
 __device__ __forceinline__ df mulf(df a, float b) {
   const float p = a.h * b;
   const float e = fmaf(a.l, b, fmaf(a.h, b, -p));
-  return quick2(p, e);
+  return dfm(p, e);
 }
 __device__ __forceinline__ df scale2(df a, float pow2) { return dfm(a.h * pow2, a.l * pow2); }  // exact
 

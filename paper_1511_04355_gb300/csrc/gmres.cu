@@ -245,10 +245,45 @@ __global__ void sub_widen_masked_kernel(cx<double>* r, const cx<float>* y, const
   if (t < n && mask[t / N]) r[t] = r[t] - widen(y[t]);
 }
 
-// r -= widen(y) for every entry
-__global__ void sub_widen_kernel(cx<double>* r, const cx<float>* y, int64_t n) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t < n) r[t] = r[t] - widen(y[t]);
+// Warm-start scaling, one block per frequency f: alpha = (y^H b) / (y^H y) with y = A x^ (the
+// complex scalar minimising |b - alpha y|; 0 when y = 0), then x0 = alpha x^ and r = b - alpha y.
+// r may alias b (each element is read before it is written, by the same thread).
+template <class Ry>
+__global__ void warm_scale_kernel(const cx<double>* b, const cx<Ry>* y, cx<double>* x0, cx<double>* r, int64_t N) {
+  __shared__ double s_yb_r[256], s_yb_i[256], s_yy[256];
+  const int64_t f = blockIdx.x;
+  const cx<double>* bf = b + f * N;
+  const cx<Ry>* yf = y + f * N;
+  double ybr = 0, ybi = 0, yy = 0;
+  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
+    const cx<double> bv = bf[n];
+    const double yr = (double)yf[n].r, yi = (double)yf[n].i;
+    ybr += yr * bv.r + yi * bv.i;
+    ybi += yr * bv.i - yi * bv.r;
+    yy += yr * yr + yi * yi;
+  }
+  s_yb_r[threadIdx.x] = ybr;
+  s_yb_i[threadIdx.x] = ybi;
+  s_yy[threadIdx.x] = yy;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) {
+      s_yb_r[threadIdx.x] += s_yb_r[threadIdx.x + k];
+      s_yb_i[threadIdx.x] += s_yb_i[threadIdx.x + k];
+      s_yy[threadIdx.x] += s_yy[threadIdx.x + k];
+    }
+    __syncthreads();
+  }
+  const double d = s_yy[0];
+  const cx<double> alpha = d > 0 ? mk(s_yb_r[0] / d, s_yb_i[0] / d) : mk(0.0, 0.0);
+  cx<double>* xf = x0 + f * N;
+  cx<double>* rf = r + f * N;
+  for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
+    const cx<double> yv = mk((double)yf[n].r, (double)yf[n].i);
+    const cx<double> bv = bf[n];
+    xf[n] = alpha * xf[n];
+    rf[n] = bv - alpha * yv;
+  }
 }
 
 // r = b - Ax  (for active instances)
@@ -266,6 +301,7 @@ struct Work {
   cx<double>* x = nullptr;    // FP64 [F][N] solution (caller-owned)
   DevBuf b, r, Ax;            // FP64 [F][N]
   DevBuf V, z, w, u;          // T
+  DevBuf V64, z64, w64;       // FP64 inner-solve buffers of the mixed path's fallback
   DevBuf H, cs, sn, g, hacc, dots, y;
   DevBuf hnorm2, target, inv_h, est, bn2, rn2;
   DevBuf act, part, kcols, status, nact, upd;
@@ -295,7 +331,7 @@ struct Ops<double> {
 // One GMRES(m) cycle on A M^{-1} y = r for the instances flagged in `part` (device), starting
 // from x = 0 of the correction; adds the correction to x64.  Returns iterations performed.
 template <class T>
-int gmres_cycle(bem_ctx* ctx, Work& W, int64_t F, int64_t N, int m,
+int gmres_cycle(bem_ctx* ctx, Work& W, DevBuf& Vb, DevBuf& zb, DevBuf& wb, int64_t F, int64_t N, int m,
                 std::vector<int32_t>& iters_host, const std::vector<int32_t>& part_h) {
   cudaStream_t st = ctx->stream;
   const int m1 = m + 1;
@@ -313,9 +349,9 @@ int gmres_cycle(bem_ctx* ctx, Work& W, int64_t F, int64_t N, int m,
   s.status = W.status.as<int32_t>();
   s.est = W.est.as<double>();
   s.nact = W.nact.as<int32_t>();
-  cx<T>* V = W.V.as<cx<T>>();
-  cx<T>* z = W.z.as<cx<T>>();
-  cx<T>* w = W.w.as<cx<T>>();
+  cx<T>* V = Vb.as<cx<T>>();
+  cx<T>* z = zb.as<cx<T>>();
+  cx<T>* w = wb.as<cx<T>>();
   const int32_t* part = W.part.as<int32_t>();
   int32_t* act = W.act.as<int32_t>();
   BEM_CUDA(cudaMemcpyAsync(act, part, sizeof(int32_t) * F, cudaMemcpyDeviceToDevice, st));
@@ -383,11 +419,11 @@ int gmres_cycle(bem_ctx* ctx, Work& W, int64_t F, int64_t N, int m,
 }
 
 template <class T>
-void reserve_inner(Work& W, int64_t F, int64_t N, int m) {
+void reserve_inner(DevBuf& V, DevBuf& z, DevBuf& w, int64_t F, int64_t N, int m) {
   const int m1 = m + 1;
-  W.V.reserve(sizeof(cx<T>) * F * m1 * N);
-  W.z.reserve(sizeof(cx<T>) * F * N);
-  W.w.reserve(sizeof(cx<T>) * F * N);
+  V.reserve(sizeof(cx<T>) * F * m1 * N);
+  z.reserve(sizeof(cx<T>) * F * N);
+  w.reserve(sizeof(cx<T>) * F * N);
 }
 
 }  // namespace
@@ -406,8 +442,8 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
   W.r.reserve(sizeof(cx<double>) * F * N);
   W.Ax.reserve(sizeof(cx<double>) * F * N);
   W.x = x_dev;
-  if (mixed) reserve_inner<float>(W, F, N, m);
-  else reserve_inner<double>(W, F, N, m);
+  if (mixed) reserve_inner<float>(W.V, W.z, W.w, F, N, m);
+  else reserve_inner<double>(W.V, W.z, W.w, F, N, m);
   W.H.reserve(sizeof(cx<double>) * F * m1 * m);
   W.cs.reserve(sizeof(double) * F * m);
   W.sn.reserve(sizeof(cx<double>) * F * m);
@@ -442,19 +478,21 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
   }
   const bool warm = o.warm_start != BEM_WARM_ZERO && ctx->warm.N == N && !ctx->warm.s.empty();
   if (warm) {
-    // x0 from the warm start; r = b - A x0 with the operator of the inner solve's precision
-    warm_initial(ctx, o.warm_start, x_dev);
+    // direction x^ from the warm start, y = A x^ with the operator of the inner solve's
+    // precision, then x0 = alpha x^ and r = b - alpha y with the alpha minimising |r|
+    warm_initial(ctx, o.warm_start, ctx->fs.s.data(), F, x_dev);
     if (mixed) {
       DevBuf xf, yf;
       xf.reserve(sizeof(cx<float>) * F * N);
       yf.reserve(sizeof(cx<float>) * F * N);
       narrow_array(ctx, x_dev, xf.as<cx<float>>(), F * N);
       apply_operator32(ctx, xf.as<cx<float>>(), yf.as<cx<float>>(), BEM_APPLY_A, nullptr);
-      sub_widen_kernel<<<grid_for(F * N, 256), 256, 0, st>>>(W.r.as<cx<double>>(), yf.as<cx<float>>(), F * N);
+      warm_scale_kernel<float><<<(unsigned)F, 256, 0, st>>>(W.r.as<cx<double>>(), yf.as<cx<float>>(), x_dev,
+                                                             W.r.as<cx<double>>(), N);
     } else {
       apply_operator64(ctx, x_dev, W.Ax.as<cx<double>>(), BEM_APPLY_A, nullptr);
-      residual_kernel<<<grid_for(F * N, 256), 256, 0, st>>>(W.b.as<cx<double>>(), W.Ax.as<cx<double>>(),
-                                                            W.r.as<cx<double>>(), N, F, nullptr);
+      warm_scale_kernel<double><<<(unsigned)F, 256, 0, st>>>(W.b.as<cx<double>>(), W.Ax.as<cx<double>>(), x_dev,
+                                                              W.r.as<cx<double>>(), N);
     }
     ctx->launches++;
     BEM_LAUNCHED();
@@ -476,6 +514,8 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
   status.assign(F, BEM_ERR_NOT_CONVERGED);
   std::vector<char> done(F, 0);
   std::vector<char> full_done(F, 0);  // the full residual has been formed once
+  std::vector<char> use64(F, 0);      // mixed path: FP64 inner solves after a stalled refinement
+  std::vector<double> prev_rel(F, 1.0);
   for (int64_t f = 0; f < F; ++f)
     if (bn2[f] == 0.0) {  // zero right-hand side: x = 0 is exact
       done[f] = 1;
@@ -495,10 +535,30 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
     }
     if (nwork == 0) break;
     if (total_inner >= o.max_iters) break;
-    BEM_CUDA(cudaMemcpyAsync(W.part.p, part.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
     BEM_CUDA(cudaMemcpyAsync(W.target.p, tgt.data(), sizeof(double) * F, cudaMemcpyHostToDevice, st));
-    int it = mixed ? gmres_cycle<float>(ctx, W, F, N, m, iters, part)
-                   : gmres_cycle<double>(ctx, W, F, N, m, iters, part);
+    int it = 0;
+    if (!mixed) {
+      BEM_CUDA(cudaMemcpyAsync(W.part.p, part.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
+      it = gmres_cycle<double>(ctx, W, W.V, W.z, W.w, F, N, m, iters, part);
+    } else {
+      // FP32 inner solves, except for frequencies whose refinement stalled: FP64 ones for those
+      std::vector<int32_t> p32(F, 0), p64(F, 0);
+      int64_t n64 = 0;
+      for (int64_t f = 0; f < F; ++f) {
+        (use64[f] ? p64 : p32)[f] = part[f];
+        n64 += part[f] && use64[f];
+      }
+      if (n64 < nwork) {
+        BEM_CUDA(cudaMemcpyAsync(W.part.p, p32.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
+        it = gmres_cycle<float>(ctx, W, W.V, W.z, W.w, F, N, m, iters, p32);
+      }
+      if (n64 > 0) {
+        reserve_inner<double>(W.V64, W.z64, W.w64, F, N, m);
+        BEM_CUDA(cudaMemcpyAsync(W.part.p, p64.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
+        it = std::max(it, gmres_cycle<double>(ctx, W, W.V64, W.z64, W.w64, F, N, m, iters, p64));
+      }
+      BEM_CUDA(cudaMemcpyAsync(W.part.p, part.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
+    }
     total_inner += it;
     BEM_CUDA(cudaMemcpyAsync(est.data(), W.est.p, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
     BEM_CUDA(cudaMemcpyAsync(stat.data(), W.status.p, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, st));
@@ -532,14 +592,14 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
     BEM_CUDA(cudaMemcpyAsync(W.part.p, part.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
     {
       std::vector<int32_t> upd(F);
-      for (int64_t f = 0; f < F; ++f) upd[f] = (part[f] && full_done[f]) ? 1 : 0;
+      for (int64_t f = 0; f < F; ++f) upd[f] = (part[f] && full_done[f] && !use64[f]) ? 1 : 0;
       BEM_CUDA(cudaMemcpyAsync(W.upd.p, upd.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
     }
     std::vector<int32_t> rlist, ulist, flist;
     for (int64_t f = 0; f < F; ++f)
       if (part[f]) {
         rlist.push_back((int32_t)f);
-        (full_done[f] ? ulist : flist).push_back((int32_t)f);
+        (full_done[f] && !use64[f] ? ulist : flist).push_back((int32_t)f);
       }
     if (rlist.empty()) break;
     // First refinement step of a frequency: the full FP64-class residual r = b - A x.  Later
@@ -580,7 +640,12 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
       } else if (rel <= o.tol) {
         done[f] = 1;
         status[f] = 0;
+      } else if (mixed && refines[f] >= 2 && rel > 0.5 * prev_rel[f]) {
+        // refinement stalled: the FP32 operator is not accurate enough for this frequency
+        // (|A - A_32| |A^{-1}| near 1); its inner solves run in FP64 from now on
+        use64[f] = 1;
       }
+      prev_rel[f] = rel;
     }
   }
 }

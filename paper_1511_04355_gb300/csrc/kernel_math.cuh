@@ -103,6 +103,50 @@ __device__ __forceinline__ void phase_exps(cx<double> zs, cx<double> zp, double,
   Ep = exp_neg(zp);
 }
 
+// E_s = e^{-z_s}, E_p = e^{-z_p} at distance r.  r_lo: low part of the distance (float-float
+// distance in the FP32 kernels, 0 otherwise); amp_s/amp_p >= 0: precomputed amplitudes
+// e^{-Re z} (FP32 kernels, common Re s)
+template <class R>
+__device__ __forceinline__ void radial_exps(R r, const FreqC<R>& fc, const MatC<R>& m, R r_lo, float amp_s,
+                                            float amp_p, cx<R>& Es, cx<R>& Ep) {
+  const cx<R> zs = r * fc.a;
+  const cx<R> zp = m.beta * zs;
+  if constexpr (sizeof(R) == 4) {
+    if (amp_s >= 0.f) {
+      const float ps = fc.ai_hi * r;
+      const float ps_lo = fmaf(fc.ai_hi, r, -ps) + fmaf(fc.ai_hi, r_lo, fc.ai_lo * r);
+      const float pp = fc.bi_hi * r;
+      const float pp_lo = fmaf(fc.bi_hi, r, -pp) + fmaf(fc.bi_hi, r_lo, fc.bi_lo * r);
+      Es = cis_neg_ff(amp_s, ps, ps_lo);
+      Ep = cis_neg_ff(amp_p, pp, pp_lo);
+      return;
+    }
+  }
+  phase_exps(zs, zp, r, r_lo, fc, Es, Ep);
+}
+// The rest of the radial part from given E_s, E_p.
+template <class R>
+__device__ __forceinline__ Radial<R> radial_given(R r, R inv_r2, const FreqC<R>& fc, const MatC<R>& m,
+                                                  cx<R> Es, cx<R> Ep) {
+  Radial<R> o;
+  const cx<R> zs = r * fc.a;
+  const cx<R> zp = m.beta * zs;
+  o.Es = Es;
+  o.gs = cfma(zs, Es, Es);
+  o.gp = cfma(zp, Ep, Ep);
+  o.P = axpy(-m.beta2, Ep, Es);
+  const R z2 = r * r * fc.a_abs2;
+  if (z2 < R(kZSeries2)) {
+    constexpr int NS = NSeries<R>::n;
+    cx<R> acc = mk(m.d[NS - 1], R(0));
+#pragma unroll
+    for (int k = NS - 2; k >= 0; --k) acc = cfma(acc, zs, mk(m.d[k], R(0)));
+    o.J = acc;
+  } else {
+    o.J = inv_r2 * ((o.gp - o.gs) * fc.inv_a2);
+  }
+  return o;
+}
 // r_lo: low part of the distance (float-float distance in the FP32 kernels, 0 otherwise);
 // amp_s/amp_p > 0: precomputed amplitudes e^{-Re z} (FP32 kernels, common Re s)
 template <class R>

@@ -3,15 +3,21 @@
 //
 // Memory: solutions x(s_j) of solved frequencies (FP64 on the device).
 // POD:    Phi = the r leading left singular vectors of X = [x(s_1) .. x(s_J)]: Gram matrix
-//         G = X^H X on the device (FP64), eigenpairs of G on the host (cyclic Jacobi on the real
-//         symmetric embedding [[Re G, -Im G], [Im G, Re G]]), Phi_k = X v_k / sigma_k.
+//         G = X^H X on the device (FP64), eigenpairs of G on the host (cyclic complex Jacobi with
+//         a relative stopping test), Phi_k = X v_k / sigma_k; r is the
+//         smallest rank whose discarded energy is <= energy_tol * trace(G).  The Gram route
+//         resolves sigma_k only down to ~1e-8 sigma_1, so energy_tol must stay well above 1e-16.
 // MLP:    u = (Re s, Im s) / Omega -> 128 -> 128 -> 2r (tanh-GELU), trained on the device to
-//         predict c_j = Phi^H x(s_j) (scaled) with MSE loss and Adam: FP32 master weights; the
+//         predict the direction of c_j = Phi^H x(s_j): c_j / |c_j| turned so that its first entry
+//         is real and non-negative.  Each target then has unit size whatever |x(s_j)|, which the
+//         FP16 products need: solution norms span decades over a frequency band, and a common
+//         scale would leave the small ones below FP16 resolution.  MSE loss and Adam: FP32 master weights; the
 //         three dense layers' products run on the tensor cores (mma.sync m16n8k16, FP16
 //         operands, FP32 accumulation), elementwise parts in FP32.  The products are tiny
 //         (at most 256 x 128 x 256), so one warp computes one 16 x 8 output tile.
-// Warm start: x0(s) = Phi c(s) (BEM_WARM_MLP) or the stored solution at the nearest solved
-//         frequency (BEM_WARM_NEAREST).
+// Warm start: the direction x^(s) = Phi c(s) (BEM_WARM_MLP) or the stored solution at the
+//         nearest solved frequency (BEM_WARM_NEAREST); the solver scales it by the complex alpha
+//         minimising |b - alpha A x^| (warm_scale).
 #include <algorithm>
 #include <chrono>
 #include <cuda_fp16.h>
@@ -195,22 +201,20 @@ __global__ void combine_basis_kernel(const cx<double>* X, const cx<double>* V, i
   Phi[t] = s;
 }
 
-// x0[f][n] = scale * sum_k (y[f][k] + i y[f][r + k]) Phi[k][n]
-__global__ void expand_kernel(const float* y, const cx<double>* Phi, int64_t N, int r, int F, double scale,
-                              cx<double>* x0) {
+// x0[f][n] = sum_k (y[f][k] + i y[f][r + k]) Phi[k][n]
+__global__ void expand_kernel(const float* y, const cx<double>* Phi, int64_t N, int r, int F, cx<double>* x0) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= N * F) return;
   const int f = (int)(t / N);
   const int64_t n = t % N;
   cx<double> s = mk(0.0, 0.0);
   for (int k = 0; k < r; ++k)
-    s = cfma(mk((double)y[f * 2 * r + k] * scale, (double)y[f * 2 * r + r + k] * scale), Phi[(int64_t)k * N + n], s);
+    s = cfma(mk((double)y[f * 2 * r + k], (double)y[f * 2 * r + r + k]), Phi[(int64_t)k * N + n], s);
   x0[t] = s;
 }
 
-// targets T[j][k] = [Re c, Im c] / scale, c = Phi^H x_j (one block per (j, k))
-__global__ void project_kernel(const cx<double>* Phi, const cx<double>* X, int64_t N, int r, double inv_scale,
-                               float* T) {
+// C[j][k] = (Phi^H x_j)_k (one block per (j, k))
+__global__ void project_kernel(const cx<double>* Phi, const cx<double>* X, int64_t N, int r, cx<double>* C) {
   __shared__ double sr[256], si[256];
   const int j = blockIdx.x, k = blockIdx.y;
   double a = 0, b = 0;
@@ -229,55 +233,60 @@ __global__ void project_kernel(const cx<double>* Phi, const cx<double>* X, int64
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    T[j * 2 * r + k] = (float)(sr[0] * inv_scale);
-    T[j * 2 * r + r + k] = (float)(si[0] * inv_scale);
-  }
+  if (threadIdx.x == 0) C[j * r + k] = mk(sr[0], si[0]);
 }
 
 // ------------------------------------------------------------------------------- host helpers
 namespace {
 
-// Eigen-decomposition of a real symmetric n x n matrix by cyclic Jacobi rotations (row-major);
-// returns eigenvalues, eigenvectors in the columns of V.
-void jacobi_eig(int n, std::vector<double>& A, std::vector<double>& w, std::vector<double>& V) {
-  V.assign((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
-  auto a = [&](int i, int j) -> double& { return A[(size_t)i * n + j]; };
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0, tot = 0;
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        tot += a(i, j) * a(i, j);
-        if (i != j) off += a(i, j) * a(i, j);
-      }
-    if (off <= 1e-30 * tot) break;
+// Eigen-decomposition of a Hermitian n x n matrix (row-major) by cyclic complex Jacobi
+// rotations: eigenvalues in w, eigenvectors in the columns of V.  A pair (p, q) is rotated while
+// |a_pq| > 1e-15 sqrt(a_pp a_qq) (a relative criterion, so that small eigenvalues of a Gram
+// matrix keep high relative accuracy, Demmel and Veselic), until a sweep rotates nothing.
+// Rotation: with a_pq = m e^{i phi}, R = diag(1, e^{-i phi}) P(theta), P the real Jacobi rotation
+// that annihilates the now real off-diagonal entry m; A <- R^H A R, V <- V R.
+void hermitian_jacobi(int n, std::vector<cx<double>>& A, std::vector<double>& w, std::vector<cx<double>>& V) {
+  V.assign((size_t)n * n, mk(0.0, 0.0));
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = mk(1.0, 0.0);
+  auto a = [&](int i, int j) -> cx<double>& { return A[(size_t)i * n + j]; };
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    bool rotated = false;
     for (int p = 0; p < n - 1; ++p)
       for (int q = p + 1; q < n; ++q) {
-        const double apq = a(p, q);
-        if (std::fabs(apq) < 1e-300) continue;
-        const double theta = (a(q, q) - a(p, p)) / (2.0 * apq);
+        const cx<double> apq = a(p, q);
+        const double m = std::hypot(apq.r, apq.i);
+        const double app = a(p, p).r, aqq = a(q, q).r;
+        if (m <= 1e-300 || m <= 1e-15 * std::sqrt(std::fabs(app * aqq))) continue;
+        rotated = true;
+        const cx<double> ph = mk(apq.r / m, apq.i / m);  // e^{i phi}
+        const cx<double> phc = conj(ph);
+        const double theta = (aqq - app) / (2.0 * m);
         const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < n; ++k) {  // columns p, q
-          const double akp = a(k, p), akq = a(k, q);
-          a(k, p) = c * akp - s * akq;
-          a(k, q) = s * akp + c * akq;
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < n; ++k) {  // columns: A R
+          const cx<double> akp = a(k, p), akq = phc * a(k, q);
+          a(k, p) = c * akp - sn * akq;
+          a(k, q) = sn * akp + c * akq;
         }
-        for (int k = 0; k < n; ++k) {  // rows p, q
-          const double apk = a(p, k), aqk = a(q, k);
-          a(p, k) = c * apk - s * aqk;
-          a(q, k) = s * apk + c * aqk;
+        for (int k = 0; k < n; ++k) {  // rows: R^H (A R)
+          const cx<double> apk = a(p, k), aqk = ph * a(q, k);
+          a(p, k) = c * apk - sn * aqk;
+          a(q, k) = sn * apk + c * aqk;
         }
-        for (int k = 0; k < n; ++k) {
-          const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
-          V[(size_t)k * n + p] = c * vkp - s * vkq;
-          V[(size_t)k * n + q] = s * vkp + c * vkq;
+        a(p, q) = mk(0.0, 0.0);
+        a(q, p) = mk(0.0, 0.0);
+        a(p, p).i = 0.0;
+        a(q, q).i = 0.0;
+        for (int k = 0; k < n; ++k) {  // V R
+          const cx<double> vkp = V[(size_t)k * n + p], vkq = phc * V[(size_t)k * n + q];
+          V[(size_t)k * n + p] = c * vkp - sn * vkq;
+          V[(size_t)k * n + q] = sn * vkp + c * vkq;
         }
       }
+    if (!rotated) break;
   }
   w.resize(n);
-  for (int i = 0; i < n; ++i) w[i] = a(i, i);
+  for (int i = 0; i < n; ++i) w[i] = a(i, i).r;
 }
 
 int64_t n_params(int r) { return 2 * kHidden + kHidden + kHidden * kHidden + kHidden + 2 * r * kHidden + 2 * r; }
@@ -383,62 +392,85 @@ void warm_train(bem_ctx* ctx, const bem_warm_params& prm, bem_warm_stats* out) {
   ctx->launches++;
   std::vector<cx<double>> Gh((size_t)J * J);
   copy_out(ctx, Gh.data(), G.p, sizeof(cx<double>) * J * J);
-  const int n2 = 2 * J;
-  std::vector<double> A((size_t)n2 * n2), w, V;
-  for (int a = 0; a < J; ++a)
-    for (int b = 0; b < J; ++b) {
-      const cx<double> g = Gh[(size_t)a * J + b];
-      A[(size_t)a * n2 + b] = g.r;
-      A[(size_t)a * n2 + J + b] = -g.i;
-      A[(size_t)(J + a) * n2 + b] = g.i;
-      A[(size_t)(J + a) * n2 + J + b] = g.r;
-    }
-  jacobi_eig(n2, A, w, V);
-  // each eigenvalue of G appears twice in the embedding; take every other one, descending
-  std::vector<int> order(n2);
-  for (int i = 0; i < n2; ++i) order[i] = i;
+  std::vector<double> w;
+  std::vector<cx<double>> V;
+  std::vector<cx<double>> Gw(Gh);
+  hermitian_jacobi(J, Gw, w, V);
+  std::vector<int> order(J);
+  for (int i = 0; i < J; ++i) order[i] = i;
   std::sort(order.begin(), order.end(), [&](int a, int b) { return w[a] > w[b]; });
+  double total = 0;  // trace(G) = sum_k sigma_k^2
+  for (int j = 0; j < J; ++j) total += Gh[(size_t)j * J + j].r;
   std::vector<int> pick;
-  std::vector<std::vector<cx<double>>> vecs;
-  const double lmax = std::max(w[order[0]], 1e-300);
+  double kept = 0;
   for (int idx : order) {
-    if ((int)pick.size() >= prm.r_max) break;
-    if (w[idx] <= prm.rel_tol * prm.rel_tol * lmax) break;
-    std::vector<cx<double>> v(J);
-    for (int j = 0; j < J; ++j) v[j] = mk(V[(size_t)j * n2 + idx], V[(size_t)(J + j) * n2 + idx]);
-    // drop the partner (i * v) of an eigenvector already taken
-    bool dup = false;
-    for (const auto& u : vecs) {
-      double pr = 0, pi = 0;
-      for (int j = 0; j < J; ++j) {
-        pr += u[j].r * v[j].r + u[j].i * v[j].i;
-        pi += u[j].r * v[j].i - u[j].i * v[j].r;
-      }
-      if (pr * pr + pi * pi > 0.5) dup = true;
-    }
-    if (dup) continue;
-    double nv = 0;
-    for (int j = 0; j < J; ++j) nv += v[j].r * v[j].r + v[j].i * v[j].i;
-    nv = std::sqrt(nv);
-    for (int j = 0; j < J; ++j) v[j] = mk(v[j].r / nv, v[j].i / nv);
-    vecs.push_back(v);
+    if ((int)pick.size() >= prm.r_max || w[idx] <= 0.0) break;
+    if (total - kept <= prm.energy_tol * total) break;
     pick.push_back(idx);
+    kept += w[idx];
   }
   const int r = (int)pick.size();
   BEM_REQUIRE(r >= 1, "POD found no basis vector");
   std::vector<cx<double>> Vs((size_t)J * r);
   for (int k = 0; k < r; ++k) {
-    const double sg = std::sqrt(std::max(w[pick[k]], 1e-300));
-    for (int j = 0; j < J; ++j) Vs[(size_t)j * r + k] = mk(vecs[k][j].r / sg, vecs[k][j].i / sg);
+    const double sg = std::sqrt(w[pick[k]]);
+    for (int j = 0; j < J; ++j) {
+      const cx<double> v = V[(size_t)j * J + pick[k]];
+      Vs[(size_t)j * r + k] = mk(v.r / sg, v.i / sg);
+    }
   }
   DevBuf dV;
   dV.reserve(sizeof(cx<double>) * J * r);
   copy_in(ctx, dV.p, Vs.data(), sizeof(cx<double>) * J * r);
-  ws.Phi.reserve(sizeof(cx<double>) * r * N);
+  DevBuf Phi0;
+  Phi0.reserve(sizeof(cx<double>) * r * N);
   combine_basis_kernel<<<grid_for(N * r, 256), 256, 0, st>>>(ws.X.as<cx<double>>(), dV.as<cx<double>>(), N, J, r,
-                                                              ws.Phi.as<cx<double>>());
+                                                              Phi0.as<cx<double>>());
   BEM_LAUNCHED();
   ctx->launches++;
+  // The Gram matrix carries rounding ~eps sigma_1^2, so X v_k / sigma_k is orthonormal only to
+  // ~eps sigma_1^2 / sigma_r^2.  One Cholesky pass restores it: M = Phi^H Phi = L L^H,
+  // Phi <- Phi L^{-H} (same subspace).
+  {
+    DevBuf dM;
+    dM.reserve(sizeof(cx<double>) * r * r);
+    gram_kernel<<<dim3(r, r), 256, 0, st>>>(Phi0.as<cx<double>>(), N, r, dM.as<cx<double>>());
+    BEM_LAUNCHED();
+    ctx->launches++;
+    std::vector<cx<double>> M((size_t)r * r), L((size_t)r * r, mk(0.0, 0.0)), Li((size_t)r * r, mk(0.0, 0.0));
+    copy_out(ctx, M.data(), dM.p, sizeof(cx<double>) * r * r);
+    for (int j = 0; j < r; ++j) {
+      double d = M[(size_t)j * r + j].r;
+      for (int k = 0; k < j; ++k) d -= L[(size_t)j * r + k].r * L[(size_t)j * r + k].r + L[(size_t)j * r + k].i * L[(size_t)j * r + k].i;
+      BEM_REQUIRE(d > 0, "POD basis re-orthonormalisation failed");
+      const double ljj = std::sqrt(d);
+      L[(size_t)j * r + j] = mk(ljj, 0.0);
+      for (int i = j + 1; i < r; ++i) {
+        cx<double> v = M[(size_t)i * r + j];
+        for (int k = 0; k < j; ++k) v = v - L[(size_t)i * r + k] * conj(L[(size_t)j * r + k]);
+        L[(size_t)i * r + j] = mk(v.r / ljj, v.i / ljj);
+      }
+    }
+    for (int c = 0; c < r; ++c)  // columns of L^{-1} by forward substitution
+      for (int i = c; i < r; ++i) {
+        cx<double> v = mk(i == c ? 1.0 : 0.0, 0.0);
+        for (int k = c; k < i; ++k) v = v - L[(size_t)i * r + k] * Li[(size_t)k * r + c];
+        const double lii = L[(size_t)i * r + i].r;
+        Li[(size_t)i * r + c] = mk(v.r / lii, v.i / lii);
+      }
+    std::vector<cx<double>> T((size_t)r * r);  // T = L^{-H}: T[j][k] = conj(Li[k][j])
+    for (int j = 0; j < r; ++j)
+      for (int k = 0; k < r; ++k) T[(size_t)j * r + k] = conj(Li[(size_t)k * r + j]);
+    DevBuf dTr;
+    dTr.reserve(sizeof(cx<double>) * r * r);
+    copy_in(ctx, dTr.p, T.data(), sizeof(cx<double>) * r * r);
+    ws.Phi.reserve(sizeof(cx<double>) * r * N);
+    combine_basis_kernel<<<grid_for(N * r, 256), 256, 0, st>>>(Phi0.as<cx<double>>(), dTr.as<cx<double>>(), N, r, r,
+                                                                ws.Phi.as<cx<double>>());
+    BEM_LAUNCHED();
+    ctx->launches++;
+    BEM_CUDA(cudaStreamSynchronize(st));
+  }
   ws.r = r;
   // training set: features and scaled targets
   double omega = 0;
@@ -450,17 +482,36 @@ void warm_train(bem_ctx* ctx, const bem_warm_params& prm, bem_warm_stats* out) {
     Uh[2 * j] = (float)(ws.s[2 * j] / omega);
     Uh[2 * j + 1] = (float)(ws.s[2 * j + 1] / omega);
   }
-  // scale: largest coefficient magnitude (sigma_1 bounds |c| per snapshot)
-  ws.scale = std::sqrt(std::max(w[pick[0]], 1e-300));
-  DevBuf dU, dT, dY, dG, dM, dVv, dloss;
+  DevBuf dU, dT, dY, dG, dM, dVv, dloss, dC;
   dU.reserve(sizeof(float) * 2 * J);
   dT.reserve(sizeof(float) * 2 * r * J);
   dY.reserve(sizeof(float) * 2 * r * J);
+  dC.reserve(sizeof(cx<double>) * r * J);
   copy_in(ctx, dU.p, Uh.data(), sizeof(float) * 2 * J);
-  project_kernel<<<dim3(J, r), 256, 0, st>>>(ws.Phi.as<cx<double>>(), ws.X.as<cx<double>>(), N, r, 1.0 / ws.scale,
-                                              dT.as<float>());
+  project_kernel<<<dim3(J, r), 256, 0, st>>>(ws.Phi.as<cx<double>>(), ws.X.as<cx<double>>(), N, r,
+                                              dC.as<cx<double>>());
   BEM_LAUNCHED();
   ctx->launches++;
+  // targets: unit-norm coefficient directions with a real non-negative leading entry
+  std::vector<cx<double>> Ch((size_t)r * J);
+  copy_out(ctx, Ch.data(), dC.p, sizeof(cx<double>) * r * J);
+  std::vector<float> Th((size_t)2 * r * J);
+  for (int j = 0; j < J; ++j) {
+    const cx<double>* c = &Ch[(size_t)j * r];
+    double nrm = 0;
+    for (int k = 0; k < r; ++k) nrm += c[k].r * c[k].r + c[k].i * c[k].i;
+    nrm = std::sqrt(nrm);
+    const double a0 = std::hypot(c[0].r, c[0].i);
+    // multiplier conj(c_0) / (|c_0| |c|): unit norm, leading entry real and >= 0
+    cx<double> m = mk(nrm > 0 ? 1.0 / nrm : 1.0, 0.0);
+    if (a0 > 0 && nrm > 0) m = mk(c[0].r / (a0 * nrm), -c[0].i / (a0 * nrm));
+    for (int k = 0; k < r; ++k) {
+      const cx<double> t = c[k] * m;
+      Th[(size_t)j * 2 * r + k] = (float)t.r;
+      Th[(size_t)j * 2 * r + r + k] = (float)t.i;
+    }
+  }
+  copy_in(ctx, dT.p, Th.data(), sizeof(float) * 2 * r * J);
   // parameters: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases, seeded
   const int64_t np = n_params(r);
   std::vector<float> ph(np, 0.f);
@@ -509,15 +560,15 @@ void warm_train(bem_ctx* ctx, const bem_warm_params& prm, bem_warm_stats* out) {
   }
 }
 
-// x0[f] for the frequencies of the current set (device [F][N]).
-void warm_initial(bem_ctx* ctx, int mode, cx<double>* x0) {
+// Warm-start directions x^[f] (device [F][N]) for the F frequencies s (host, 2F doubles).
+void warm_initial(bem_ctx* ctx, int mode, const double* s, int64_t F, cx<double>* x0) {
   WarmStart& ws = ctx->warm;
-  const int64_t F = ctx->fs.F, N = 3 * ctx->mesh.ne;
+  const int64_t N = 3 * ctx->mesh.ne;
   BEM_REQUIRE(ws.N == N && !ws.s.empty(), "warm start requested but no stored solutions match the mesh");
   if (mode == BEM_WARM_NEAREST) {
     const int J = (int)(ws.s.size() / 2);
     for (int64_t f = 0; f < F; ++f) {
-      const double sr = ctx->fs.s[2 * f], si = ctx->fs.s[2 * f + 1];
+      const double sr = s[2 * f], si = s[2 * f + 1];
       int best = 0;
       double bd = 1e300;
       for (int j = 0; j < J; ++j) {
@@ -535,8 +586,8 @@ void warm_initial(bem_ctx* ctx, int mode, cx<double>* x0) {
   BEM_REQUIRE(ws.trained, "BEM_WARM_MLP requested before bem_warm_train");
   std::vector<float> Uh(2 * F);
   for (int64_t f = 0; f < F; ++f) {
-    Uh[2 * f] = (float)(ctx->fs.s[2 * f] / ws.omega);
-    Uh[2 * f + 1] = (float)(ctx->fs.s[2 * f + 1] / ws.omega);
+    Uh[2 * f] = (float)(s[2 * f] / ws.omega);
+    Uh[2 * f + 1] = (float)(s[2 * f + 1] / ws.omega);
   }
   DevBuf dU, dY;
   dU.reserve(sizeof(float) * 2 * F);
@@ -544,7 +595,7 @@ void warm_initial(bem_ctx* ctx, int mode, cx<double>* x0) {
   copy_in(ctx, dU.p, Uh.data(), sizeof(float) * 2 * F);
   mlp_pass(ctx, ws.params.as<float>(), ws.r, dU.as<float>(), (int)F, nullptr, dY.as<float>(), nullptr, nullptr);
   expand_kernel<<<grid_for(N * F, 256), 256, 0, ctx->stream>>>(dY.as<float>(), ws.Phi.as<cx<double>>(), N, ws.r,
-                                                                (int)F, ws.scale, x0);
+                                                                (int)F, x0);
   BEM_LAUNCHED();
   ctx->launches++;
 }

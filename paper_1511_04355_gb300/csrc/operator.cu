@@ -13,6 +13,8 @@
 //   near_kernel  : for sources in the near list, the 7-point rule minus the 4-point rule (the
 //                  far kernel already added the latter), plus the own-element 3x3 block.
 //   precond      : right block-Jacobi, y_i = A_ii^{-1} x_i.
+#include <algorithm>
+
 #include "kernel_math.cuh"
 
 namespace bem {
@@ -44,6 +46,7 @@ struct FarArgs {
   double* yacc;                 // [F][ne][3] complex FP64 accumulator (atomic adds)
   const FreqC<R>* fc;           // [F]
   const int32_t* flist;         // frequencies to compute (the active ones), nfl entries
+  const FarGroup* groups;       // recurrence kernel: one per blockIdx.y, its run of list entries
   int64_t nfl;
   int64_t chunk;                // sources per split (multiple of the tile size)
   int64_t ne, F;
@@ -137,8 +140,40 @@ __device__ __forceinline__ void u_contract(const Radial<R>& K, R cu, R rh0, R rh
 // per source column.  Residual mode (RESID = true): y = K k - A x with k = profile(s) * known
 // data; every source contributes through both kernels, T applied to vT and U to vU where
 // (vT, vU) = (-x_e, k_e) for traction-given and (-k_e, x_e) for displacement-given columns.
-template <class R, int TB, int S, int FT, bool RESID>
-__global__ void __launch_bounds__(TB) far_kernel(const FarArgs<R> a) {
+// e^{-i theta} with theta = (w_hi + w_lo)(r + r_lo), |theta| <= 1.5 (the host admits a group
+// only then): theta in float-float, cos and sin of its high part by their Taylor series (terms
+// to theta^12 / theta^13, truncation < 4e-9), the low part added to first order.  Accurate to
+// about an ulp: the recurrence multiplies this factor up to FT - 1 times.
+__device__ __forceinline__ cx<float> step_factor(float w_hi, float w_lo, float r, float r_lo) {
+  const float th = w_hi * r;
+  const float tl = fmaf(w_hi, r, -th) + fmaf(w_hi, r_lo, w_lo * r);
+  const float t = th * th;
+  float c = fmaf(t, 1.f / 479001600.f, -1.f / 3628800.f);
+  c = fmaf(t, c, 1.f / 40320.f);
+  c = fmaf(t, c, -1.f / 720.f);
+  c = fmaf(t, c, 1.f / 24.f);
+  c = fmaf(t, c, -0.5f);
+  c = fmaf(t, c, 1.f);
+  float sn = fmaf(t, -1.f / 6227020800.f, 1.f / 39916800.f);
+  sn = fmaf(t, sn, -1.f / 362880.f);
+  sn = fmaf(t, sn, 1.f / 5040.f);
+  sn = fmaf(t, sn, -1.f / 120.f);
+  sn = fmaf(t, sn, 1.f / 6.f);
+  sn = fmaf(-t * th, sn, th);
+  // cos(th + tl) ~ c - sn tl, sin(th + tl) ~ sn + c tl
+  return mk(fmaf(-sn, tl, c), -fmaf(c, tl, sn));
+}
+
+// BEM_FAR_MIN_BLOCKS (optional, build flag): compile the far kernels for that many resident CTAs
+// per SM (a register cap); unset, the compiler chooses.
+#ifdef BEM_FAR_MIN_BLOCKS
+#define BEM_FAR_BOUNDS(TB) __launch_bounds__(TB, BEM_FAR_MIN_BLOCKS)
+#else
+#define BEM_FAR_BOUNDS(TB) __launch_bounds__(TB)
+#endif
+
+template <class R, int TB, int S, int FT, bool RESID, bool REC>
+__global__ void BEM_FAR_BOUNDS(TB) far_kernel(const FarArgs<R> a) {
   using V = typename V4<R>::T;
   constexpr int NV = RESID ? 7 : 4;                                    // cx per (source, freq)
   constexpr bool FF = sizeof(R) == 4;                                  // float-float distances
@@ -154,8 +189,12 @@ __global__ void __launch_bounds__(TB) far_kernel(const FarArgs<R> a) {
   FreqC<R>* sfc = reinterpret_cast<FreqC<R>*>(sv + NV * FT * S);      // [FT]
 
   const int tid = threadIdx.x;
-  const int64_t g0 = (int64_t)blockIdx.y * FT;   // position in the frequency list
-  const int nf = (int)min((int64_t)FT, a.nfl - g0);
+  // the CTA's frequencies: FT consecutive list entries per blockIdx.y, or (recurrence kernel) the
+  // run its group descriptor names
+  FarGroup grp{};
+  if constexpr (REC) grp = a.groups[blockIdx.y];
+  const int64_t g0 = REC ? (int64_t)grp.start : (int64_t)blockIdx.y * FT;
+  const int nf = REC ? grp.count : (int)min((int64_t)FT, a.nfl - g0);
   const unsigned mask = (1u << nf) - 1u;
   const int64_t src0 = (int64_t)blockIdx.z * a.chunk;
   const int64_t src1 = min(a.ne, src0 + a.chunk);
@@ -184,6 +223,8 @@ __global__ void __launch_bounds__(TB) far_kernel(const FarArgs<R> a) {
   for (int k = 1; k < nf; ++k) same_re = same_re && (float)sfc[k].a.r == (float)sfc[0].a.r;
   const float re_s = FF ? -(float)sfc[0].a.r : 0.f;
   const float re_p = FF ? -(float)(sfc[0].a.r * m.beta) : 0.f;
+  // equally spaced group (FP32): E(s_j) = E(s_{j-1}) e^{-i delta r / c}, one complex product
+  // per exponential instead of a range reduction and a sine/cosine
   const R inv4pi = R(kInv4Pi);
 
   for (int64_t e0 = src0; e0 < src1; e0 += S) {
@@ -263,12 +304,33 @@ __global__ void __launch_bounds__(TB) far_kernel(const FarArgs<R> a) {
           amp_s = __expf(re_s * (float)r);
           amp_p = __expf(re_p * (float)r);
         }
+        cx<R> ws = mk(R(1), R(0)), wp = ws, Es = ws, Ep = ws;
+        if constexpr (REC) {  // one-step factors e^{-i delta r / c_s}, e^{-i beta delta r / c_s}
+          ws = step_factor(grp.ws_hi, grp.ws_lo, (float)r, (float)r_lo);
+          wp = step_factor(grp.wp_hi, grp.wp_lo, (float)r, (float)r_lo);
+        }
+        // E_s, E_p of group member k: in an equally spaced group by the one-step product from
+        // member k - 1, else directly
+        auto exps = [&](int k) {
+          if (REC && k > 0) {
+            Es = Es * ws;
+            Ep = Ep * wp;
+          } else {
+            radial_exps(r, sfc[k], m, r_lo, amp_s, amp_p, Es, Ep);
+          }
+        };
         if (RESID || !isU) {
 #pragma unroll
           for (int k = 0; k < FT; ++k) {
             if (!((mask >> k) & 1u)) continue;
             const cx<R>* v = sv + NV * (e * FT + k);
-            const Radial<R> K = radial(r, inv_r2, sfc[k], m, r_lo, amp_s, amp_p);
+            Radial<R> K;
+            if constexpr (REC) {
+              exps(k);
+              K = radial_given(r, inv_r2, sfc[k], m, Es, Ep);
+            } else {
+              K = radial(r, inv_r2, sfc[k], m, r_lo, amp_s, amp_p);
+            }
             const TCoef<R> T = tcoef(K, m);
             t_contract(T, cw, drdn, rh0, rh1, rh2, nn.x, nn.y, nn.z, v[0], v[1], v[2], v[3], part[k]);
             if (RESID) u_contract(K, cu, rh0, rh1, rh2, v[4], v[5], v[6], part[k]);
@@ -278,7 +340,13 @@ __global__ void __launch_bounds__(TB) far_kernel(const FarArgs<R> a) {
           for (int k = 0; k < FT; ++k) {
             if (!((mask >> k) & 1u)) continue;
             const cx<R>* v = sv + NV * (e * FT + k);
-            const Radial<R> K = radial(r, inv_r2, sfc[k], m, r_lo, amp_s, amp_p);
+            Radial<R> K;
+            if constexpr (REC) {
+              exps(k);
+              K = radial_given(r, inv_r2, sfc[k], m, Es, Ep);
+            } else {
+              K = radial(r, inv_r2, sfc[k], m, r_lo, amp_s, amp_p);
+            }
             u_contract(K, cu, rh0, rh1, rh2, v[0], v[1], v[2], part[k]);
           }
         }
@@ -486,7 +554,14 @@ struct Cfg<double> {  // FP64: 128 targets x 4 frequencies per CTA, 32-element s
 
 // Device copy of the frequency list (all frequencies when `flist` is null) and the FP64
 // far-field accumulator, zeroed for the listed frequencies.
-int64_t stage_flist(bem_ctx* ctx, const std::vector<int32_t>* flist) {
+// Device copy of the frequency list (all frequencies when `flist` is null), its grouping into
+// CTA frequency groups, and the FP64 far-field accumulator zeroed for the listed frequencies.
+// rec_ft > 0 (FP32 operator): the list is reordered into equally spaced runs of at least 4
+// frequencies (groups of at most rec_ft, for the recurrence kernel) followed by the remaining
+// frequencies (FT per CTA); a run qualifies when its frequencies share Re s, their Im s steps
+// agree to 1e-12 relative (FP64) and one step's phase (Im delta / c_s) x the mesh's
+// bounding-box diagonal is at most 1.5.  rec_ft = 0: list order, FT per CTA.
+int64_t stage_flist(bem_ctx* ctx, const std::vector<int32_t>* flist, int rec_ft) {
   const int64_t F = ctx->fs.F, ne = ctx->mesh.ne;
   std::vector<int32_t>& h = ctx->flist_h;
   if (flist) h = *flist;
@@ -495,23 +570,78 @@ int64_t stage_flist(bem_ctx* ctx, const std::vector<int32_t>* flist) {
     for (int64_t f = 0; f < F; ++f) h[f] = (int32_t)f;
   }
   const int64_t n = (int64_t)h.size();
+  std::vector<FarGroup>& gr = ctx->groups_h;
+  gr.clear();
+  ctx->rec_entries = 0;
+  if (rec_ft > 0 && n > 0) {
+    const std::vector<double>& s = ctx->fs.s;
+    const MatC<double> m = mat_constants64(ctx->mat);
+    std::vector<int32_t> rec, rest;
+    std::vector<FarGroup> rg;
+    int64_t i = 0;
+    while (i < n) {
+      int64_t j = i + 1;
+      double d = 0.0;
+      if (i + 1 < n) {
+        const double re0 = s[2 * h[i]], im0 = s[2 * h[i] + 1];
+        d = s[2 * h[i + 1] + 1] - im0;
+        const bool small = std::fabs(d * m.inv_cs) * ctx->mesh.diam <= 1.5;
+        if (d != 0.0 && small && s[2 * h[i + 1]] == re0) {
+          j = i + 2;
+          while (j < n && j - i < rec_ft && s[2 * h[j]] == re0 &&
+                 std::fabs((s[2 * h[j] + 1] - im0) - (double)(j - i) * d) <= 1e-12 * std::fabs(s[2 * h[j] + 1]))
+            ++j;
+        }
+      }
+      if (j - i >= 4) {
+        FarGroup g{};
+        g.start = (int32_t)rec.size();
+        g.count = (int32_t)(j - i);
+        const double ws = d * m.inv_cs, wp = ws * m.beta;
+        g.ws_hi = (float)ws;
+        g.ws_lo = (float)(ws - (double)g.ws_hi);
+        g.wp_hi = (float)wp;
+        g.wp_lo = (float)(wp - (double)g.wp_hi);
+        rg.push_back(g);
+        for (int64_t k = i; k < j; ++k) rec.push_back(h[k]);
+        i = j;
+      } else {
+        rest.push_back(h[i]);
+        ++i;
+      }
+    }
+    gr = rg;
+    ctx->rec_entries = (int64_t)rec.size();
+    h = rec;
+    h.insert(h.end(), rest.begin(), rest.end());
+  }
   ctx->flist_d.reserve(sizeof(int32_t) * std::max<int64_t>(n, 1));
+  ctx->groups_d.reserve(sizeof(FarGroup) * std::max<size_t>(gr.size(), 1));
   ctx->yacc.reserve(sizeof(double) * 6 * F * ne);
   if (n) BEM_CUDA(cudaMemcpyAsync(ctx->flist_d.p, h.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+  if (!gr.empty())
+    BEM_CUDA(cudaMemcpyAsync(ctx->groups_d.p, gr.data(), sizeof(FarGroup) * gr.size(), cudaMemcpyHostToDevice,
+                             ctx->stream));
   // zero the accumulator rows of the listed frequencies (contiguous runs in one memset each)
+  std::vector<int32_t> sorted(h);
+  std::sort(sorted.begin(), sorted.end());
   for (int64_t a = 0; a < n;) {
     int64_t b = a + 1;
-    while (b < n && h[b] == h[b - 1] + 1) ++b;
-    BEM_CUDA(cudaMemsetAsync(ctx->yacc.as<double>() + (int64_t)h[a] * ne * 6, 0,
+    while (b < n && sorted[b] == sorted[b - 1] + 1) ++b;
+    BEM_CUDA(cudaMemsetAsync(ctx->yacc.as<double>() + (int64_t)sorted[a] * ne * 6, 0,
                              sizeof(double) * 6 * ne * (b - a), ctx->stream));
     a = b;
   }
   return n;
 }
 
-template <class R, bool RESID>
-static void launch_far(bem_ctx* ctx, const cx<R>* x, int which, int64_t nfl) {
+// One far-field launch.  REC: over the group descriptors [g0, g0 + ng); else over the list
+// entries [off, off + nfl), FT per CTA.
+template <class R, bool RESID, bool REC>
+static void launch_far_part(bem_ctx* ctx, const cx<R>* x, int which, int64_t off, int64_t nfl, int64_t g0,
+                            int64_t ng) {
   constexpr int TB = Cfg<R>::TB, S = Cfg<R>::S, FT = Cfg<R>::FT;
+  if (nfl <= 0) return;
   FarArgs<R> a;
   a.bcv = ctx->bc.set ? ctx->bc.d_value.as<double>() : nullptr;
   a.pfac = ctx->fs.pfac.as<cx<double>>();
@@ -525,13 +655,14 @@ static void launch_far(bem_ctx* ctx, const cx<R>* x, int which, int64_t nfl) {
   a.x = x;
   a.yacc = ctx->yacc.as<double>();
   a.fc = Geo<R>::fc(ctx);
-  a.flist = ctx->flist_d.as<int32_t>();
+  a.flist = ctx->flist_d.as<int32_t>() + off;
+  a.groups = REC ? ctx->groups_d.as<FarGroup>() + g0 : nullptr;
   a.nfl = nfl;
   a.ne = ctx->mesh.ne;
   a.F = ctx->fs.F;
   a.m = Geo<R>::m(ctx);
   // split the sources so that the grid covers about four waves of resident CTAs
-  const int64_t tb = grid_for(a.ne, TB), groups = grid_for(nfl, FT);
+  const int64_t tb = grid_for(a.ne, TB), groups = REC ? ng : grid_for(nfl, FT);
   // and so that a CTA sums at most 8 source tiles in R precision before the FP64 atomic add
   const int64_t want = 4 * 152 * Cfg<R>::kPerSM;
   int64_t nsplit = std::max<int64_t>(1, (want + tb * groups - 1) / (tb * groups));
@@ -542,13 +673,26 @@ static void launch_far(bem_ctx* ctx, const cx<R>* x, int which, int64_t nfl) {
   nsplit = (a.ne + chunk - 1) / chunk;
   a.chunk = chunk;
   const size_t smem = far_smem<R, TB, S, FT, RESID>();
-  BEM_CUDA(cudaFuncSetAttribute(far_kernel<R, TB, S, FT, RESID>,
+  BEM_CUDA(cudaFuncSetAttribute(far_kernel<R, TB, S, FT, RESID, REC>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const dim3 grid((unsigned)tb, (unsigned)groups, (unsigned)nsplit);
   ProfScope ps(ctx, RESID ? PK_RES64 : (sizeof(R) == 4 ? PK_FAR32 : PK_FAR64), nfl);
-  far_kernel<R, TB, S, FT, RESID><<<grid, TB, smem, ctx->stream>>>(a);
+  far_kernel<R, TB, S, FT, RESID, REC><<<grid, TB, smem, ctx->stream>>>(a);
   BEM_LAUNCHED();
   ctx->launches++;
+}
+
+// Far field over the staged list: FP32 equally spaced runs (the leading rec_entries) by the
+// recurrence kernel, the rest by the direct one.
+template <class R, bool RESID>
+static void launch_far(bem_ctx* ctx, const cx<R>* x, int which, int64_t nfl) {
+  const int64_t nrec = ctx->rec_entries;
+  if constexpr (sizeof(R) == 4 && !RESID) {
+    launch_far_part<R, RESID, true>(ctx, x, which, 0, nrec, 0, (int64_t)ctx->groups_h.size());
+    launch_far_part<R, RESID, false>(ctx, x, which, nrec, nfl - nrec, 0, 0);
+  } else {
+    launch_far_part<R, RESID, false>(ctx, x, which, 0, nfl, 0, 0);
+  }
 }
 
 template <class R>
@@ -584,7 +728,7 @@ static void launch_near(bem_ctx* ctx, const cx<R>* x, cx<R>* y, int which, int64
 
 void apply_operator64(bem_ctx* ctx, const cx<double>* x, cx<double>* y, int which,
                       const std::vector<int32_t>* flist) {
-  const int64_t n = stage_flist(ctx, flist);
+  const int64_t n = stage_flist(ctx, flist, 0);
   if (!n) return;
   launch_far<double, false>(ctx, x, which, n);
   launch_near<double>(ctx, x, y, which, n, false);
@@ -597,7 +741,7 @@ void near_residual64(bem_ctx* ctx, const cx<double>* x, cx<double>* r, int64_t n
 
 void residual64(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::vector<int32_t>* flist) {
   BEM_REQUIRE(ctx->bc.set, "residual needs boundary conditions");
-  const int64_t n = stage_flist(ctx, flist);
+  const int64_t n = stage_flist(ctx, flist, 0);
   if (!n) return;
   launch_far<double, true>(ctx, x, BEM_APPLY_A, n);
   launch_near<double>(ctx, x, r, BEM_APPLY_A, n, true);
@@ -606,7 +750,7 @@ void residual64(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::vec
 
 void apply_operator32(bem_ctx* ctx, const cx<float>* x, cx<float>* y, int which,
                       const std::vector<int32_t>* flist) {
-  const int64_t n = stage_flist(ctx, flist);
+  const int64_t n = stage_flist(ctx, flist, Cfg<float>::FT);
   if (!n) return;
   launch_far<float, false>(ctx, x, which, n);
   launch_near<float>(ctx, x, y, which, n, false);

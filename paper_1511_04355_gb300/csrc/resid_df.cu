@@ -212,8 +212,8 @@ __global__ void __launch_bounds__(kTB) resid_df_kernel(const ResDfArgs a) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             float* pc = pa + (4 * c) * TB;
-            const df re = add(dfm(pc[0], pc[TB]), oc[c].r);
-            const df im = add(dfm(pc[2 * TB], pc[3 * TB]), oc[c].i);
+            const df re = add_n(dfm(pc[0], pc[TB]), oc[c].r);
+            const df im = add_n(dfm(pc[2 * TB], pc[3 * TB]), oc[c].i);
             pc[0] = re.h;
             pc[TB] = re.l;
             pc[2 * TB] = im.h;
@@ -260,7 +260,7 @@ DfConst make_df_const() {
 // field and own element in FP64.
 void residual_df(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::vector<int32_t>* flist) {
   BEM_REQUIRE(ctx->bc.set, "residual needs boundary conditions");
-  const int64_t nfl = stage_flist(ctx, flist);
+  const int64_t nfl = stage_flist(ctx, flist, 0);
   if (!nfl) return;
   const MatC<double> md = mat_constants64(ctx->mat);
   ResDfArgs a;

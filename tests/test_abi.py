@@ -56,3 +56,8 @@ def test_calls_without_gpu_return_error_codes():
     assert lib.bem_solve_frequencies(None, None, 0, None, None) == P.BEM_ERR_INVALID_ARG
     opt = P.bem_options()
     assert lib.bem_default_options(ctypes.byref(opt)) == 0 and opt.tol == 1e-6 and opt.restart == 50
+    # batch driver: argument checks happen before any worker starts or any CUDA call
+    assert lib.bem_solve_batch(None, 1, 0) == P.BEM_ERR_INVALID_ARG
+    items = (P.bem_batch_item * 2)()
+    assert lib.bem_solve_batch(items, 2, 0) == P.BEM_ERR_INVALID_ARG       # null contexts
+    assert lib.bem_solve_batch(items, 0, 0) == P.BEM_ERR_INVALID_ARG
