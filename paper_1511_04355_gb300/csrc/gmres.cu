@@ -514,7 +514,6 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
   status.assign(F, BEM_ERR_NOT_CONVERGED);
   std::vector<char> done(F, 0);
   std::vector<char> full_done(F, 0);  // the full residual has been formed once
-  std::vector<char> use64(F, 0);      // mixed path: FP64 inner solves after a stalled refinement
   std::vector<double> prev_rel(F, 1.0);
   for (int64_t f = 0; f < F; ++f)
     if (bn2[f] == 0.0) {  // zero right-hand side: x = 0 is exact
@@ -522,45 +521,77 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
       resid[f] = 0.0;
       status[f] = 0;
     }
-  const int max_outer = mixed ? std::max(1, o.max_refine) : std::max(1, o.max_iters / m + 1);
+
+  // Plain FP64 GMRES(m) on the frequencies not done: restarted cycles, each accepted when the FP64
+  // GMRES residual estimate meets the tolerance, else restarted from the true FP64 residual.
+  auto fp64_loop = [&](DevBuf& Vb, DevBuf& zb, DevBuf& wb) {
+    const int max_cycles = std::max(1, o.max_iters / m + 1);
+    int total = 0;
+    for (int cycle = 0; cycle < max_cycles; ++cycle) {
+      int64_t nwork = 0;
+      for (int64_t f = 0; f < F; ++f) {
+        part[f] = done[f] ? 0 : 1;
+        nwork += part[f];
+        tgt[f] = 0.999 * o.tol * std::sqrt(bn2[f]);
+      }
+      if (nwork == 0 || total >= o.max_iters) break;
+      BEM_CUDA(cudaMemcpyAsync(W.target.p, tgt.data(), sizeof(double) * F, cudaMemcpyHostToDevice, st));
+      BEM_CUDA(cudaMemcpyAsync(W.part.p, part.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
+      total += gmres_cycle<double>(ctx, W, Vb, zb, wb, F, N, m, iters, part);
+      BEM_CUDA(cudaMemcpyAsync(est.data(), W.est.p, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
+      BEM_CUDA(cudaMemcpyAsync(stat.data(), W.status.p, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, st));
+      BEM_CUDA(cudaStreamSynchronize(st));
+      std::vector<int32_t> rlist;
+      for (int64_t f = 0; f < F; ++f) {
+        if (!part[f]) continue;
+        const double rel = est[f] / std::sqrt(bn2[f]);
+        resid[f] = rel;
+        if (stat[f] == BEM_ERR_BREAKDOWN) {
+          done[f] = 1;
+          status[f] = BEM_ERR_BREAKDOWN;
+        } else if (est[f] <= o.tol * std::sqrt(bn2[f])) {
+          done[f] = 1;
+          status[f] = 0;
+        } else {
+          rlist.push_back((int32_t)f);
+        }
+        part[f] = done[f] ? 0 : 1;
+      }
+      if (rlist.empty()) break;
+      // restart from the true residual
+      BEM_CUDA(cudaMemcpyAsync(W.part.p, part.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
+      residual64(ctx, x_dev, W.r.as<cx<double>>(), &rlist);
+      norm2_kernel<double><<<(unsigned)F, 256, 0, st>>>(W.r.as<cx<double>>(), N, W.part.as<int32_t>(),
+                                                        W.rn2.as<double>());
+      ctx->launches++;
+      BEM_LAUNCHED();
+      for (int32_t f : rlist) refines[f]++;
+    }
+  };
+
+  if (!mixed) {
+    fp64_loop(W.V, W.z, W.w);
+    return;
+  }
+
+  // Mixed: FP32 inner GMRES(m) solves to a relative inner tolerance, each followed by an
+  // FP64-class residual, until that residual meets the tolerance.
+  std::vector<char> fallback(F, 0);
+  const int max_outer = std::max(1, o.max_refine);
   int total_inner = 0;
   for (int outer = 0; outer < max_outer; ++outer) {
-    // who still needs work
     int64_t nwork = 0;
     for (int64_t f = 0; f < F; ++f) {
       part[f] = done[f] ? 0 : 1;
       nwork += part[f];
       const double rn = std::sqrt(rn2[f]), bnrm = std::sqrt(bn2[f]);
-      tgt[f] = mixed ? std::max(o.inner_tol * rn, 0.25 * o.tol * bnrm) : 0.999 * o.tol * bnrm;
+      tgt[f] = std::max(o.inner_tol * rn, 0.25 * o.tol * bnrm);
     }
     if (nwork == 0) break;
     if (total_inner >= o.max_iters) break;
     BEM_CUDA(cudaMemcpyAsync(W.target.p, tgt.data(), sizeof(double) * F, cudaMemcpyHostToDevice, st));
-    int it = 0;
-    if (!mixed) {
-      BEM_CUDA(cudaMemcpyAsync(W.part.p, part.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
-      it = gmres_cycle<double>(ctx, W, W.V, W.z, W.w, F, N, m, iters, part);
-    } else {
-      // FP32 inner solves, except for frequencies whose refinement stalled: FP64 ones for those
-      std::vector<int32_t> p32(F, 0), p64(F, 0);
-      int64_t n64 = 0;
-      for (int64_t f = 0; f < F; ++f) {
-        (use64[f] ? p64 : p32)[f] = part[f];
-        n64 += part[f] && use64[f];
-      }
-      if (n64 < nwork) {
-        BEM_CUDA(cudaMemcpyAsync(W.part.p, p32.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
-        it = gmres_cycle<float>(ctx, W, W.V, W.z, W.w, F, N, m, iters, p32);
-      }
-      if (n64 > 0) {
-        reserve_inner<double>(W.V64, W.z64, W.w64, F, N, m);
-        BEM_CUDA(cudaMemcpyAsync(W.part.p, p64.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
-        it = std::max(it, gmres_cycle<double>(ctx, W, W.V64, W.z64, W.w64, F, N, m, iters, p64));
-      }
-      BEM_CUDA(cudaMemcpyAsync(W.part.p, part.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
-    }
-    total_inner += it;
-    BEM_CUDA(cudaMemcpyAsync(est.data(), W.est.p, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
+    BEM_CUDA(cudaMemcpyAsync(W.part.p, part.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
+    total_inner += gmres_cycle<float>(ctx, W, W.V, W.z, W.w, F, N, m, iters, part);
     BEM_CUDA(cudaMemcpyAsync(stat.data(), W.status.p, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, st));
     BEM_CUDA(cudaStreamSynchronize(st));
     for (int64_t f = 0; f < F; ++f)
@@ -569,37 +600,18 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
         part[f] = 0;
         status[f] = BEM_ERR_BREAKDOWN;
       }
-    if (!mixed) {
-      // plain FP64: accept the FP64 GMRES residual estimate when it meets the tolerance;
-      // otherwise restart from the true residual.
-      bool need_restart = false;
-      for (int64_t f = 0; f < F; ++f) {
-        if (!part[f]) continue;
-        const double rel = est[f] / std::sqrt(bn2[f]);
-        if (est[f] <= o.tol * std::sqrt(bn2[f])) {
-          done[f] = 1;
-          part[f] = 0;
-          resid[f] = rel;
-          status[f] = 0;
-        } else {
-          need_restart = true;
-          resid[f] = rel;
-        }
-      }
-      if (!need_restart) break;
-    }
     // FP64-class residual r = b - A x for the instances still working
     BEM_CUDA(cudaMemcpyAsync(W.part.p, part.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
     {
       std::vector<int32_t> upd(F);
-      for (int64_t f = 0; f < F; ++f) upd[f] = (part[f] && full_done[f] && !use64[f]) ? 1 : 0;
+      for (int64_t f = 0; f < F; ++f) upd[f] = (part[f] && full_done[f]) ? 1 : 0;
       BEM_CUDA(cudaMemcpyAsync(W.upd.p, upd.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
     }
     std::vector<int32_t> rlist, ulist, flist;
     for (int64_t f = 0; f < F; ++f)
       if (part[f]) {
         rlist.push_back((int32_t)f);
-        (full_done[f] && !use64[f] ? ulist : flist).push_back((int32_t)f);
+        (full_done[f] ? ulist : flist).push_back((int32_t)f);
       }
     if (rlist.empty()) break;
     // First refinement step of a frequency: the full FP64-class residual r = b - A x.  Later
@@ -607,19 +619,13 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
     // inner solve's precision: d is small (|d| ~ kappa |r| / |A|), so the product's rounding,
     // ~eps_32 |A| |d|, stays ~1e-10 |b| below the tolerance being certified.
     if (!flist.empty()) {
-      if (mixed && o.residual_mode == BEM_RESID_DF64) residual_df(ctx, x_dev, W.r.as<cx<double>>(), &flist);
+      if (o.residual_mode == BEM_RESID_DF64) residual_df(ctx, x_dev, W.r.as<cx<double>>(), &flist);
       else residual64(ctx, x_dev, W.r.as<cx<double>>(), &flist);
     }
     if (!ulist.empty()) {
-      if (mixed) {
-        apply_operator32(ctx, W.z.as<cx<float>>(), W.w.as<cx<float>>(), BEM_APPLY_A, &ulist);
-        sub_widen_masked_kernel<<<grid_for(F * N, 256), 256, 0, st>>>(W.r.as<cx<double>>(), W.w.as<cx<float>>(),
-                                                                       W.upd.as<int32_t>(), N, F * N);
-      } else {
-        apply_operator64(ctx, W.z.as<cx<double>>(), W.Ax.as<cx<double>>(), BEM_APPLY_A, &ulist);
-        residual_kernel<<<grid_for(F * N, 256), 256, 0, st>>>(W.r.as<cx<double>>(), W.Ax.as<cx<double>>(),
-                                                              W.r.as<cx<double>>(), N, F, W.upd.as<int32_t>());
-      }
+      apply_operator32(ctx, W.z.as<cx<float>>(), W.w.as<cx<float>>(), BEM_APPLY_A, &ulist);
+      sub_widen_masked_kernel<<<grid_for(F * N, 256), 256, 0, st>>>(W.r.as<cx<double>>(), W.w.as<cx<float>>(),
+                                                                     W.upd.as<int32_t>(), N, F * N);
       ctx->launches++;
     }
     for (int32_t f : flist) full_done[f] = 1;
@@ -640,12 +646,65 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
       } else if (rel <= o.tol) {
         done[f] = 1;
         status[f] = 0;
-      } else if (mixed && refines[f] >= 2 && rel > 0.5 * prev_rel[f]) {
-        // refinement stalled: the FP32 operator is not accurate enough for this frequency
-        // (|A - A_32| |A^{-1}| near 1); its inner solves run in FP64 from now on
-        use64[f] = 1;
+      } else if (refines[f] >= 2 && rel > 0.25 * prev_rel[f]) {
+        // refinement stalled (a healthy step gains >= 10x): the FP32 operator is too inaccurate
+        // for this frequency, |A - A_32| |A^{-1}| near 1
+        done[f] = 1;
+        fallback[f] = 1;
       }
       prev_rel[f] = rel;
+    }
+  }
+  // Stalled or unconverged frequencies: a fresh FP64 solve from x = 0 (a restarted GMRES from
+  // the mixed iterate can stagnate where one from zero converges), with the FP64 right-hand side
+  // and its result certified by the native FP64 residual.
+  std::vector<int32_t> fl;
+  for (int64_t f = 0; f < F; ++f)
+    if (fallback[f] || (status[f] == BEM_ERR_NOT_CONVERGED && !done[f])) fl.push_back((int32_t)f);
+  if (fl.empty()) return;
+  for (int64_t f = 0; f < F; ++f) done[f] = 1;
+  for (int32_t f : fl) {
+    done[f] = 0;
+    part[f] = 1;
+    status[f] = BEM_ERR_NOT_CONVERGED;
+  }
+  BEM_CUDA(cudaMemcpyAsync(W.part.p, part.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
+  known_data(ctx, W.Ax.as<cx<double>>());
+  apply_operator64(ctx, W.Ax.as<cx<double>>(), W.b.as<cx<double>>(), BEM_APPLY_K, &fl);
+  for (int32_t f : fl) {
+    BEM_CUDA(cudaMemsetAsync(x_dev + (int64_t)f * N, 0, sizeof(cx<double>) * N, st));
+    BEM_CUDA(cudaMemcpyAsync(W.r.as<cx<double>>() + (int64_t)f * N, W.b.as<cx<double>>() + (int64_t)f * N,
+                             sizeof(cx<double>) * N, cudaMemcpyDeviceToDevice, st));
+  }
+  {
+    std::vector<int32_t> sel(F, 0);
+    for (int32_t f : fl) sel[f] = 1;
+    BEM_CUDA(cudaMemcpyAsync(W.part.p, sel.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
+    norm2_kernel<double><<<(unsigned)F, 256, 0, st>>>(W.b.as<cx<double>>(), N, W.part.as<int32_t>(),
+                                                      W.bn2.as<double>());
+    ctx->launches++;
+    BEM_CUDA(cudaMemcpyAsync(W.rn2.p, W.bn2.p, sizeof(double) * F, cudaMemcpyDeviceToDevice, st));
+    BEM_CUDA(cudaMemcpyAsync(bn2.data(), W.bn2.p, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
+    BEM_CUDA(cudaStreamSynchronize(st));
+  }
+  reserve_inner<double>(W.V64, W.z64, W.w64, F, N, m);
+  fp64_loop(W.V64, W.z64, W.w64);
+  // certify with the true FP64 residual
+  {
+    std::vector<int32_t> sel(F, 0);
+    for (int32_t f : fl) sel[f] = 1;
+    BEM_CUDA(cudaMemcpyAsync(W.part.p, sel.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
+    residual64(ctx, x_dev, W.r.as<cx<double>>(), &fl);
+    norm2_kernel<double><<<(unsigned)F, 256, 0, st>>>(W.r.as<cx<double>>(), N, W.part.as<int32_t>(),
+                                                      W.rn2.as<double>());
+    ctx->launches++;
+    BEM_CUDA(cudaMemcpyAsync(rn2.data(), W.rn2.p, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
+    BEM_CUDA(cudaStreamSynchronize(st));
+    for (int32_t f : fl) {
+      refines[f]++;
+      const double rel = std::sqrt(rn2[f] / bn2[f]);
+      resid[f] = rel;
+      if (status[f] != BEM_ERR_BREAKDOWN) status[f] = rel <= o.tol ? 0 : BEM_ERR_NOT_CONVERGED;
     }
   }
 }
