@@ -50,10 +50,10 @@ METRIC = "BEM frequency solves/s at 1e-6 rel. residual vs plain FP64 GPU; % FP32
 FLOPS_PER_UNIT_T = 159
 FLOPS_PER_UNIT_U = 113   # displacement-kernel (U) columns: the right-hand side pass
 FLOPS_PER_UNIT_RES = 221  # fused FP64 residual r = K k - A x: T and U per kernel evaluation
-# The same residual in float-float on the FP32 pipes (resid_df_kernel): FP32 flops per kernel
-# evaluation, FADD + FMUL + 2 FFMA thread-instructions of one launch (ncu executed-instruction
-# counters, 16 frequencies on 5120 triangles) divided by its units
-FLOPS_PER_UNIT_RES_DF = 2476
+# The same residual in float-float on the FP32 pipes (resid_df_kernel, lazily renormalised
+# pairs): FP32 flops per kernel evaluation, FADD + FMUL + 2 FFMA thread-instructions of one launch
+# (ncu executed-instruction counters, 16 frequencies on 5120 triangles) divided by its units
+FLOPS_PER_UNIT_RES_DF = 1811
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 

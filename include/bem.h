@@ -61,12 +61,12 @@ extern "C" {
 #define BEM_APPLY_K 1     /* y = K(s) x : the operator acting on the known boundary data,
                              so that b(s) = K(s) (profile(s) * pattern)                       */
 
-#define BEM_RESID_DF64 0  /* far field of the residual in float-float (~2^-46) on the FP32 pipes */
-#define BEM_RESID_FP64 1  /* far field of the residual in native FP64                          */
+#define BEM_RESID_DF64 0  /* far and near field of the residual in float-float on the FP32 pipes */
+#define BEM_RESID_FP64 1  /* far and near field of the residual in native FP64                 */
 
 #define BEM_WARM_ZERO 0     /* GMRES starts from x0 = 0                                       */
-#define BEM_WARM_NEAREST 1  /* x0 = the stored solution at the nearest solved frequency      */
-#define BEM_WARM_MLP 2      /* x0 = POD basis * MLP(s) (trained by bem_warm_train)           */
+#define BEM_WARM_NEAREST 1  /* x0 = alpha * the stored solution at the nearest frequency     */
+#define BEM_WARM_MLP 2      /* x0 = alpha * POD basis * MLP(s) (trained by bem_warm_train)   */
 
 typedef struct bem_ctx bem_ctx;
 
@@ -74,13 +74,14 @@ typedef struct bem_options {
   int32_t precision;   /* BEM_PREC_FP64 or BEM_PREC_MIXED (default MIXED)                   */
   int32_t restart;     /* GMRES restart length m (default 50)                               */
   int32_t max_iters;   /* cap on GMRES iterations per inner solve (default 500)             */
-  int32_t max_refine;  /* cap on FP64 refinement steps in MIXED mode (default 8)            */
+  int32_t max_refine;  /* cap on FP64 refinement steps in MIXED mode (default 8); a frequency
+                          whose refinement stalls (< 4x per step) or that exhausts the cap is
+                          solved again in plain FP64 from x0 = 0                             */
   double tol;          /* target ||b - A x||_2 / ||b||_2, measured in FP64 (default 1e-6)   */
   double inner_tol;    /* relative reduction asked of each FP32 inner solve (default 2e-7;
                           never below 0.25 tol of the right-hand side)                     */
   int32_t warm_start;  /* BEM_WARM_* (default ZERO)                                          */
-  int32_t freq_tile;   /* frequencies per operator tile, 0 = autotuned (default 0)          */
-  int32_t use_graph;   /* capture GMRES iterations in CUDA graphs (default 1)                */
+  int32_t reserved0[2]; /* zero                                                              */
   int32_t residual_mode; /* MIXED refinement residual: BEM_RESID_DF64 (default) or
                             BEM_RESID_FP64                                                    */
   int32_t reserved[6];
@@ -305,7 +306,11 @@ typedef struct bem_afs_params {
   int32_t nt;        /* time points of the E1 integrals (512)                             */
   int32_t max_samples; /* cap on N_c (400)                                                */
   int32_t vf_iters;  /* pole relocations per fit (20)                                     */
-  int32_t reserved[6];
+  int32_t batch;     /* new frequencies per step (1: the paper's algorithm).  b > 1 (a
+                        variant, to keep the GPU batched): the paper's s_new, then further
+                        argmaxes of the same discrepancy curve after masking +-Omega/(2J)
+                        around each pick, kept while >= 0.1 of the first; solved together    */
+  int32_t reserved[5];
 } bem_afs_params;
 
 typedef struct bem_afs_stats {

@@ -23,6 +23,12 @@ Readings where the paper is silent: the search for s_new runs over n_grid unifor
 [0, Omega] and skips grid points within 1.5 grid spacings of an existing sample; each ORF is
 scaled by its largest sampled magnitude before pole identification; the integrals of E1 are
 trapezoidal sums on a uniform grid of nt times in [0, T].
+
+Several new frequencies per step (batch > 1; a variant, not the paper's algorithm, which adds
+one): the first is the paper's s_new; each further one is the argmax of the same discrepancy
+curve after masking +-Omega / (2 J) around every frequency already picked this step (J = the
+number of samples before the step), kept only while its discrepancy is at least 0.1 of the first
+pick's; all of them are solved together.  batch = 1 is the paper's algorithm.
 """
 from __future__ import annotations
 
@@ -77,15 +83,34 @@ def _step(s, F, orf, eta, omega_max, grid, t, alpha_H, alpha_L, n_iter):
     return polesH, RH, e, diff, h
 
 
+def pick_new(grid, d, s, omega_max, batch=1):
+    """Indices of the new frequencies on the search grid from the discrepancy curve d of the
+    ORF with the largest e_k: the argmax over grid points more than 1.5 spacings from every
+    sample, then (batch > 1) further argmaxes after masking +-Omega/(2J) around each pick."""
+    dgrid = omega_max / (len(grid) - 1)
+    d = np.array(d, dtype=float)
+    taken = np.abs(grid.imag[:, None] - np.asarray(s).imag[None, :]).min(axis=1) < 1.5 * dgrid
+    d[taken] = -1.0
+    picks = [int(np.argmax(d))]
+    first = d[picks[0]]
+    half = omega_max / (2.0 * len(s))
+    while len(picks) < batch:
+        d[np.abs(grid.imag - grid.imag[picks[-1]]) <= half] = -1.0
+        g = int(np.argmax(d))
+        if d[g] < 0.1 * first or d[g] < 0:
+            break
+        picks.append(g)
+    return picks
+
+
 def run(solve, eta, omega_max, T, orf, test, J0=16, alpha_H=2.0, alpha_L=2.3, E1bar=1e-4,
-        E2bar=2e-3, Jc=3, n_grid=4096, nt=512, max_samples=400, n_iter=20):
+        E2bar=2e-3, Jc=3, n_grid=4096, nt=512, max_samples=400, n_iter=20, batch=1):
     """orf, test: column indices into the responses returned by solve."""
     orf = np.asarray(orf)
     test = np.asarray(test)
     s = chebyshev_frequencies(eta, omega_max, J0)
     F = np.asarray(solve(s))
     grid = eta + 1j * np.linspace(0.0, omega_max, n_grid)
-    dgrid = omega_max / (n_grid - 1)
     t = np.linspace(0.0, T, nt)
     E1s, E2s = [], []
     h_prev = None
@@ -106,9 +131,7 @@ def run(solve, eta, omega_max, T, orf, test, J0=16, alpha_H=2.0, alpha_L=2.3, E1
         if ok_run >= Jc + 1 or len(s) >= max_samples:
             return AFSResult(s=s, F=F, poles=polesH, R=RH, E1=E1s, E2=E2s, t=t, h=h)
         kmax = orf[np.argmax(e[orf])]
-        d = diff[:, kmax].copy()
-        taken = np.abs(grid.imag[:, None] - s.imag[None, :]).min(axis=1) < 1.5 * dgrid
-        d[taken] = -1.0
-        s_new = grid[int(np.argmax(d))]
+        picks = pick_new(grid, diff[:, kmax], s, omega_max, min(batch, max_samples - len(s)))
+        s_new = grid[picks]
         s = np.append(s, s_new)
-        F = np.vstack([F, np.asarray(solve(np.array([s_new])))])
+        F = np.vstack([F, np.asarray(solve(s_new))])

@@ -58,7 +58,7 @@ class BemError(RuntimeError):
 class bem_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("restart", C.c_int32), ("max_iters", C.c_int32),
                 ("max_refine", C.c_int32), ("tol", C.c_double), ("inner_tol", C.c_double),
-                ("warm_start", C.c_int32), ("freq_tile", C.c_int32), ("use_graph", C.c_int32),
+                ("warm_start", C.c_int32), ("reserved0", C.c_int32 * 2),
                 ("residual_mode", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
@@ -74,7 +74,7 @@ class bem_afs_params(C.Structure):
                 ("alpha_H", C.c_double), ("alpha_L", C.c_double), ("E1bar", C.c_double),
                 ("E2bar", C.c_double), ("J0", C.c_int32), ("Jc", C.c_int32), ("n_grid", C.c_int32),
                 ("nt", C.c_int32), ("max_samples", C.c_int32), ("vf_iters", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("batch", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class bem_afs_stats(C.Structure):

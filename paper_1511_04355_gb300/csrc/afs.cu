@@ -9,7 +9,9 @@
 //            observed unknowns; e_k = max|f_kH - f_kL| / max|f_kH| on a uniform grid of
 //            n_grid frequencies in [0, Omega] (Eq. (ferr)); s_new = grid argmax of
 //            |f_kH - f_kL| for the ORF k with the largest e_k (Eqs. (snew), (snew1)), skipping
-//            grid points within 1.5 spacings of a sample; E1 (Eq. (stop-E1), trapezoidal on nt
+//            grid points within 1.5 spacings of a sample (batch > 1, a variant: further
+//            argmaxes of the same curve after masking +-Omega/(2J) around each pick, kept while
+//            >= 0.1 of the first, all solved in one batch); E1 (Eq. (stop-E1), trapezoidal on nt
 //            times in [0, T], E1 = inf at the first step) and E2 = max e_k over the test
 //            unknowns (Eq. (stop-E2))
 //   stop     when E1 < E1bar and E2 < E2bar at a step and at the J_c steps that follow
@@ -103,6 +105,7 @@ int bem_default_afs_params(bem_afs_params* p) {
   p->n_grid = 4096;
   p->nt = 512;
   p->max_samples = 400;
+  p->batch = 1;
   p->vf_iters = 20;
   return BEM_OK;
 }
@@ -198,6 +201,7 @@ int bem_afs(bem_ctx* ctx, const bem_afs_params* prm, const int64_t* orf, int64_t
     BEM_REQUIRE(p.J0 >= 3 && p.alpha_H > 0 && p.alpha_L > p.alpha_H, "need J0 >= 3, 0 < alpha_H < alpha_L");
     BEM_REQUIRE(p.Jc >= 0 && p.n_grid >= 16 && p.nt >= 2 && p.max_samples >= p.J0 && p.vf_iters >= 1,
                 "bad AFS parameters");
+    BEM_REQUIRE(p.batch >= 1 && p.batch <= 64, "batch must be in [1, 64]");
     const int64_t N = 3 * ctx->mesh.ne;
     const int nobs = (int)(K + Kt);
     std::vector<int64_t> dofs(nobs);
@@ -218,7 +222,7 @@ int bem_afs(bem_ctx* ctx, const bem_afs_params* prm, const int64_t* orf, int64_t
         sr[2 * f] = sl[f].real();
         sr[2 * f + 1] = sl[f].imag();
       }
-      prepare_frequencies(ctx, sr.data(), F);
+      prepare_frequencies(ctx, sr.data(), F, ctx->opt.precision == BEM_PREC_MIXED);
       ctx->io_a.reserve(sizeof(cx<double>) * F * N);
       std::vector<int32_t> it, rf, status;
       std::vector<double> res;
@@ -274,24 +278,36 @@ int bem_afs(bem_ctx* ctx, const bem_afs_params* prm, const int64_t* orf, int64_t
       int kmax = 0;
       for (int k = 1; k < K; ++k)
         if (so.e[k] > so.e[kmax]) kmax = k;
-      double best = -1;
-      int gbest = 0;
+      // discrepancy curve of that ORF, grid points within 1.5 spacings of a sample excluded
+      std::vector<double> d(p.n_grid);
       for (int g = 0; g < p.n_grid; ++g) {
-        bool taken = false;
+        d[g] = so.diff[(size_t)g * nobs + kmax];
         for (const cd& sj : s)
           if (std::fabs(grid[g].imag() - sj.imag()) < 1.5 * dgrid) {
-            taken = true;
+            d[g] = -1.0;
             break;
           }
-        if (taken) continue;
-        if (so.diff[(size_t)g * nobs + kmax] > best) {
-          best = so.diff[(size_t)g * nobs + kmax];
-          gbest = g;
-        }
+      }
+      // the paper's s_new; with batch > 1 further argmaxes after masking +-Omega/(2J) around
+      // each pick, kept while at least 0.1 of the first pick's discrepancy
+      const int want = std::min(p.batch, p.max_samples - (int)s.size());
+      const double half = p.omega_max / (2.0 * (double)s.size());
+      std::vector<cd> picks;
+      double first = 0;
+      for (int b = 0; b < want; ++b) {
+        int gbest = 0;
+        for (int g = 1; g < p.n_grid; ++g)
+          if (d[g] > d[gbest]) gbest = g;
+        if (b == 0) first = d[gbest];
+        else if (d[gbest] < 0.1 * first || d[gbest] < 0) break;
+        picks.push_back(grid[gbest]);
+        const double wb = grid[gbest].imag();
+        for (int g = 0; g < p.n_grid; ++g)
+          if (std::fabs(grid[g].imag() - wb) <= half) d[g] = -1.0;
       }
       std::vector<cd> Fn;
-      solve({grid[gbest]}, Fn);
-      s.push_back(grid[gbest]);
+      solve(picks, Fn);
+      s.insert(s.end(), picks.begin(), picks.end());
       F.insert(F.end(), Fn.begin(), Fn.end());
     }
     if (resp_out && t_out && nt_out > 0) {

@@ -136,8 +136,6 @@ int bem_default_options(bem_options* o) {
   o->tol = 1e-6;
   o->inner_tol = 2e-7;
   o->warm_start = BEM_WARM_ZERO;
-  o->freq_tile = 0;
-  o->use_graph = 1;
   o->residual_mode = BEM_RESID_DF64;
   return BEM_OK;
 }
@@ -519,7 +517,7 @@ int bem_fsm(bem_ctx* ctx, double period, double eta, int64_t nc, const double* t
       s[2 * k + 1] = 2.0 * kPi * (double)k / period;
     }
     ctx->f32_applies = ctx->f64_applies = 0;
-    prepare_frequencies(ctx, s.data(), nc);
+    prepare_frequencies(ctx, s.data(), nc, ctx->opt.precision == BEM_PREC_MIXED);
     ctx->io_a.reserve(sizeof(cx<double>) * nc * N);
     std::vector<int32_t> it, rf, status;
     std::vector<double> res;
@@ -567,7 +565,7 @@ int bem_solve_frequencies(bem_ctx* ctx, const double* s, int64_t ns, double* x_o
     ctx->f32_applies = ctx->f64_applies = 0;
     std::vector<double> sh(2 * ns);
     copy_out(ctx, sh.data(), s, sizeof(double) * 2 * ns);
-    prepare_frequencies(ctx, sh.data(), ns);
+    prepare_frequencies(ctx, sh.data(), ns, ctx->opt.precision == BEM_PREC_MIXED);
     const int64_t n = ns * 3 * ctx->mesh.ne;
     ctx->io_a.reserve(sizeof(cx<double>) * n);
     std::vector<int32_t> it, rf, status;

@@ -180,6 +180,15 @@ struct Mesh {
   int64_t nnz = 0;
   std::vector<int32_t> h_near_ptr, h_near_col;
   double diam = 0;             // bounding-box diagonal (bounds every source-target distance)
+  DevBuf self_pts;             // SelfPt[ne][3 kDuffyN^2]: own-element Duffy points (float-float)
+};
+
+// One Duffy point of an element's own integral (frequency independent): distance r, unit
+// direction rh and weight w, each as a float-float pair (hi, lo).
+struct SelfPt {
+  float4 a;  // r_hi, r_lo, rh0_hi, rh0_lo
+  float4 b;  // rh1_hi, rh1_lo, rh2_hi, rh2_lo
+  float2 c;  // w_hi, w_lo
 };
 
 struct Material {
@@ -273,7 +282,9 @@ void build_geometry(bem_ctx* ctx);
 void build_near_lists(bem_ctx* ctx);
 MatC<double> mat_constants64(const Material& m);
 MatC<float> mat_constants32(const Material& m);
-void prepare_frequencies(bem_ctx* ctx, const double* s_host, int64_t F);
+// df_self: form the own-element Duffy sums in float-float (mixed-precision solves, whose
+// FP64-class residual tolerates ~1e-12 block errors); else in FP64 (FP64 solves, parity checks).
+void prepare_frequencies(bem_ctx* ctx, const double* s_host, int64_t F, bool df_self = false);
 void element_blocks(bem_ctx* ctx, double sr, double si, const int32_t* rows,
                     const int32_t* cols, int64_t npairs, cx<double>* H, cx<double>* G);
 
@@ -289,6 +300,9 @@ void residual64(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::vec
 // the same with the far field in float-float arithmetic on the FP32 pipes (resid_df.cu)
 void residual_df(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::vector<int32_t>* flist);
 void build_freq_df(bem_ctx* ctx, const double* s, int64_t F);
+// own-element Duffy sums in float-float: out[F][ne][13] = (psi, chi rh rh (6), T remainder a (3),
+// b (3)) per frequency and element (resid_df.cu)
+void self_sums_df(bem_ctx* ctx, cx<double>* out);
 // helpers shared by the far kernels: stage the frequency list + zero the FP64 accumulator, and
 // the FP64 near-field/own-element pass of the residual
 int64_t stage_flist(bem_ctx* ctx, const std::vector<int32_t>* flist, int rec_ft);

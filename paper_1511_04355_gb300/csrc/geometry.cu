@@ -178,6 +178,8 @@ __global__ void geometry_kernel(GeoArgs a) {
   }
 }
 
+__global__ void self_pts_kernel(const Elem64* elem, const double* tri64, int64_t ne, SelfPt* out);
+
 void build_geometry(bem_ctx* ctx) {
   Mesh& m = ctx->mesh;
   const int64_t ne = m.ne, nv = (int64_t)m.verts.size() / 3;
@@ -232,6 +234,12 @@ void build_geometry(bem_ctx* ctx) {
   if (bad) throw Error(BEM_ERR_INVALID_ARG, "degenerate (zero-area) triangle " + std::to_string(bad - 1));
   BEM_CUDA(cudaMemcpyToSymbolAsync(c_gl, R.gl, sizeof R.gl, 0, cudaMemcpyHostToDevice, ctx->stream));
   BEM_CUDA(cudaMemcpyToSymbolAsync(c_glw, R.glw, sizeof R.glw, 0, cudaMemcpyHostToDevice, ctx->stream));
+  const int64_t npts = ne * 3 * kDuffyN * kDuffyN;
+  m.self_pts.reserve(sizeof(SelfPt) * npts);
+  self_pts_kernel<<<grid_for(npts, 128), 128, 0, ctx->stream>>>(m.elem64.as<Elem64>(), m.tri64.as<double>(), ne,
+                                                                 m.self_pts.as<SelfPt>());
+  BEM_LAUNCHED();
+  ctx->launches++;
 }
 
 // ------------------------------------------------------------------------------- near lists
@@ -356,7 +364,42 @@ struct SelfArgs {
   cx<float>* Minv32;   // [F][ne][9] (nullable)
   const int32_t* idx;  // optional element list (element_blocks); null = all
   int* singular;       // set when a diagonal block is singular
+  const cx<double>* sums;  // [F][ne][13] Duffy sums formed in float-float (nullable: FP64 here)
 };
+
+// Own-element Duffy points of every element (frequency independent), FP64, stored as
+// float-float pairs for the float-float sums: thread (i, t), t over the 3 kDuffyN^2 points of
+// the three sub-triangles around the centroid.
+__global__ void self_pts_kernel(const Elem64* elem, const double* tri64, int64_t ne, SelfPt* out) {
+  constexpr int NPT = kDuffyN * kDuffyN;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= ne * 3 * NPT) return;
+  const int64_t i = g / (3 * NPT);
+  const int t = (int)(g % (3 * NPT));
+  const int sub = t / NPT, k = t % NPT, iu = k / kDuffyN, iv = k % kDuffyN;
+  const double u = c_gl[iu], v = c_gl[iv];
+  const Elem64 el = elem[i];
+  double ea[3], eb[3], d[3];
+  for (int c = 0; c < 3; ++c) {
+    const double va = tri64[9 * i + 3 * sub + c], vb = tri64[9 * i + 3 * ((sub + 1) % 3) + c];
+    ea[c] = va - el.c[c];
+    eb[c] = vb - va;
+    d[c] = u * ea[c] + u * v * eb[c];
+  }
+  const double cr0 = ea[1] * eb[2] - ea[2] * eb[1], cr1 = ea[2] * eb[0] - ea[0] * eb[2],
+               cr2 = ea[0] * eb[1] - ea[1] * eb[0];
+  const double wq = c_glw[iu] * c_glw[iv] * u * sqrt(cr0 * cr0 + cr1 * cr1 + cr2 * cr2);
+  const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  const double rinv = rsqrt(r2), r = r2 * rinv;
+  auto hi = [](double x) { return __double2float_rn(x); };
+  auto lo = [](double x) { return __double2float_rn(x - (double)__double2float_rn(x)); };
+  const double rh0 = d[0] * rinv, rh1 = d[1] * rinv, rh2 = d[2] * rinv;
+  SelfPt o;
+  o.a = make_float4(hi(r), lo(r), hi(rh0), lo(rh0));
+  o.b = make_float4(hi(rh1), lo(rh1), hi(rh2), lo(rh2));
+  o.c = make_float2(hi(wq), lo(wq));
+  out[g] = o;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -405,6 +448,16 @@ __global__ void self_blocks_kernel(SelfArgs a) {
   cx<double> gpsi = mk(0.0, 0.0), gchi[6], av[3], bv[3];
   for (int k = 0; k < 6; ++k) gchi[k] = mk(0.0, 0.0);
   for (int k = 0; k < 3; ++k) av[k] = bv[k] = mk(0.0, 0.0);
+  if (a.sums) {  // the Duffy sums were formed in float-float (self_sums_df)
+    if (lane != 0) return;
+    const cx<double>* sm = a.sums + w * 13;
+    gpsi = sm[0];
+    for (int k = 0; k < 6; ++k) gchi[k] = sm[1 + k];
+    for (int k = 0; k < 3; ++k) {
+      av[k] = sm[7 + k];
+      bv[k] = sm[10 + k];
+    }
+  } else {
   constexpr int NPT = kDuffyN * kDuffyN;
   for (int t = lane; t < 3 * NPT; t += 32) {
     const int sub = t / NPT, k = t % NPT, iu = k / kDuffyN, iv = k % kDuffyN;
@@ -449,6 +502,7 @@ __global__ void self_blocks_kernel(SelfArgs a) {
     bv[k] = mk(warp_sum(bv[k].r), warp_sum(bv[k].i));
   }
   if (lane != 0) return;
+  }
   // static CPV: C_k = -sum_edges nu_k int ds / r, nu = (b - a) x n / |b - a|
   double C[3] = {0, 0, 0};
   for (int k = 0; k < 3; ++k) {
@@ -516,7 +570,7 @@ __global__ void self_blocks_kernel(SelfArgs a) {
 }
 
 // ------------------------------------------------------------------------------- frequencies
-void prepare_frequencies(bem_ctx* ctx, const double* s, int64_t F) {
+void prepare_frequencies(bem_ctx* ctx, const double* s, int64_t F, bool df_self) {
   Mesh& me = ctx->mesh;
   FreqSet& fs = ctx->fs;
   const MatC<double> m = mat_constants64(ctx->mat);
@@ -584,6 +638,13 @@ void prepare_frequencies(bem_ctx* ctx, const double* s, int64_t F) {
   a.singular = sing.as<int>();
   const int64_t threads = 32 * F * me.ne;
   ProfScope ps(ctx, PK_SELF);
+  DevBuf sums;
+  a.sums = nullptr;
+  if (df_self) {
+    sums.reserve(sizeof(cx<double>) * 13 * F * me.ne);
+    self_sums_df(ctx, sums.as<cx<double>>());
+    a.sums = sums.as<cx<double>>();
+  }
   self_blocks_kernel<<<grid_for(threads, 128), 128, 0, ctx->stream>>>(a);
   BEM_LAUNCHED();
   ctx->launches++;
@@ -718,6 +779,7 @@ void element_blocks(bem_ctx* ctx, double sr, double si, const int32_t* rows, con
     a.Minv32 = nullptr;
     a.idx = dself.as<int32_t>();
     a.singular = nullptr;
+    a.sums = nullptr;  // this verification entry point integrates in FP64
     self_blocks_kernel<<<grid_for(32 * ns, 128), 128, 0, ctx->stream>>>(a);
     BEM_LAUNCHED();
     ctx->launches++;

@@ -50,6 +50,45 @@ __device__ __forceinline__ cdf cdf_from(cx<double> z) { return cmk(df_from(z.r),
 // one complex accumulator update: o += a * v (a, v complex)
 __device__ __forceinline__ cdf cfma_df(cdf a, cdf v, cdf o) { return cadd(o, cmul(a, v)); }
 
+// One source point's contribution to r = K k - A x at a target, in float-float, from the
+// exponentials E_s, E_p and z_s, z_p: the radial algebra (J, Q, A, q1, q2; the Taylor series of
+// J for |z_s| < 0.1) and the T contraction with vT (and n.vT) plus the U contraction with vU
+// (v = vT[3], n.vT, vU[3]); cw = w/(4 pi r^2), cwd = cw dr/dn, cu = w/(4 pi mu r) carry the
+// signed weight.
+__device__ __forceinline__ void point_terms(cdf Es, cdf Ep, cdf zs, cdf zp, df inv_r2, const FreqDf& F,
+                                            const MatDf& m, df cw, df cwd, df cu, df drdn, df rx, df ry, df rz,
+                                            df n0, df n1, df n2, const cdf* v, cdf* oc) {
+  const cdf gs = cadd(Es, cmul(zs, Es));
+  const cdf gp = cadd(Ep, cmul(zp, Ep));
+  const cdf Pp = csub(Es, cscale(m.beta2, Ep));
+  cdf J;
+  if (zs.r.h * zs.r.h + zs.i.h * zs.i.h < kZSeriesDf2) {
+    J = cmk(m.d[kSeriesDf - 1], dfm(0.f, 0.f));
+#pragma unroll 1
+    for (int t = kSeriesDf - 2; t >= 0; --t) J = cadd(cmul(J, zs), cmk(m.d[t], dfm(0.f, 0.f)));
+  } else {
+    J = cscale(inv_r2, cmul(csub(gp, gs), F.inv_a2));
+  }
+  const cdf Q = csub(cscalef(6.f, J), cmk(scale2(Pp.r, 2.f), scale2(Pp.i, 2.f)));
+  const cdf A = csub(Q, gs);
+  const cdf q1 = csub(Q, cscale(m.c1m2b2, gp));
+  const cdf g2 = csub(gs, cscale(m.beta2, gp));
+  const cdf q2 = csub(cmk(scale2(g2.r, 2.f), scale2(g2.i, 2.f)), cscalef(5.f, Q));
+  // T applied to vT
+  const cdf rv = cadd(cadd(cscale(rx, v[0]), cscale(ry, v[1])), cscale(rz, v[2]));
+  const cdf t1 = cscale(cwd, A);
+  const cdf t2 = cmul(cscale(cw, A), rv);
+  const cdf t3 = cscale(cw, cadd(cmul(q1, v[3]), cscale(drdn, cmul(q2, rv))));
+  // U applied to vU
+  const cdf psi = cscale(cu, csub(Es, J));
+  const cdf ru = cadd(cadd(cscale(rx, v[4]), cscale(ry, v[5])), cscale(rz, v[6]));
+  const cdf crv = cmul(cscale(cu, csub(Pp, cscalef(3.f, J))), ru);
+  const cdf t3p = csub(t3, crv);
+  oc[0] = cadd(cadd(cmul(t1, v[0]), cmul(psi, v[4])), cadd(cscale(n0, t2), cscale(rx, t3p)));
+  oc[1] = cadd(cadd(cmul(t1, v[1]), cmul(psi, v[5])), cadd(cscale(n1, t2), cscale(ry, t3p)));
+  oc[2] = cadd(cadd(cmul(t1, v[2]), cmul(psi, v[6])), cadd(cscale(n2, t2), cscale(rz, t3p)));
+}
+
 __global__ void __launch_bounds__(kTB) resid_df_kernel(const ResDfArgs a) {
   constexpr int TB = kTB, S = kS, FT = kFT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -178,37 +217,9 @@ __global__ void __launch_bounds__(kTB) resid_df_kernel(const ResDfArgs a) {
           df_sincos(ph_p, C, sn_, cs_);
           const cdf Ep = cmk(mul(Ap, cs_), neg(mul(Ap, sn_)));
           const cdf zs = cmk(zr_s, ph_s), zp = cmk(zr_p, ph_p);
-          const cdf gs = cadd(Es, cmul(zs, Es));
-          const cdf gp = cadd(Ep, cmul(zp, Ep));
-          const cdf Pp = csub(Es, cscale(m.beta2, Ep));
-          cdf J;
-          if (zr_s.h * zr_s.h + ph_s.h * ph_s.h < kZSeriesDf2) {
-            J = cmk(m.d[kSeriesDf - 1], dfm(0.f, 0.f));
-#pragma unroll 1
-            for (int t = kSeriesDf - 2; t >= 0; --t) J = cadd(cmul(J, zs), cmk(m.d[t], dfm(0.f, 0.f)));
-          } else {
-            J = cscale(inv_r2, cmul(csub(gp, gs), F.inv_a2));
-          }
-          const cdf Q = csub(cscalef(6.f, J), cmk(scale2(Pp.r, 2.f), scale2(Pp.i, 2.f)));
-          const cdf A = csub(Q, gs);
-          const cdf q1 = csub(Q, cscale(m.c1m2b2, gp));
-          const cdf g2 = csub(gs, cscale(m.beta2, gp));
-          const cdf q2 = csub(cmk(scale2(g2.r, 2.f), scale2(g2.i, 2.f)), cscalef(5.f, Q));
-          // T applied to vT
-          const cdf rv = cadd(cadd(cscale(rx, v[0]), cscale(ry, v[1])), cscale(rz, v[2]));
-          const cdf t1 = cscale(cwd, A);
-          const cdf t2 = cmul(cscale(cw, A), rv);
-          const cdf t3 = cscale(cw, cadd(cmul(q1, v[3]), cscale(drdn, cmul(q2, rv))));
-          // U applied to vU
-          const cdf psi = cscale(cu, csub(Es, J));
-          const cdf ru = cadd(cadd(cscale(rx, v[4]), cscale(ry, v[5])), cscale(rz, v[6]));
-          const cdf crv = cmul(cscale(cu, csub(Pp, cscalef(3.f, J))), ru);
-          const cdf t3p = csub(t3, crv);
-          const cdf o0 = cadd(cadd(cmul(t1, v[0]), cmul(psi, v[4])), cadd(cscale(n0, t2), cscale(rx, t3p)));
-          const cdf o1 = cadd(cadd(cmul(t1, v[1]), cmul(psi, v[5])), cadd(cscale(n1, t2), cscale(ry, t3p)));
-          const cdf o2 = cadd(cadd(cmul(t1, v[2]), cmul(psi, v[6])), cadd(cscale(n2, t2), cscale(rz, t3p)));
+          cdf oc[3];
+          point_terms(Es, Ep, zs, zp, inv_r2, F, m, cw, cwd, cu, drdn, rx, ry, rz, n0, n1, n2, v, oc);
           float* pa = pacc + (k * 12) * TB + tid;
-          const cdf oc[3] = {o0, o1, o2};
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             float* pc = pa + (4 * c) * TB;
@@ -234,6 +245,211 @@ __global__ void __launch_bounds__(kTB) resid_df_kernel(const ResDfArgs a) {
   }
 }
 
+// Near field and own element of r = K k - A x in float-float: one thread per (listed frequency,
+// collocation point).  For every near source, the 7-point rule minus the 4-point rule the far
+// sweep already applied (the same point algebra as the far sweep); the own element through its
+// FP64 blocks, r_i += -(1/2 I + H_ii) vT_i + G_ii vU_i, in FP64.  Adds the far-field sums.
+struct NearDfArgs {
+  const D4 *q4, *q7, *cen, *nrm;  // FP64 geometry
+  const int32_t *ptr, *col;       // near lists (CSR)
+  const int8_t* bc;
+  const double* bcv;              // [ne][3]
+  const cx<double>* pfac;         // [F]
+  const cx<double>* Tself;        // [F][ne][9]
+  const cx<double>* Gself;
+  const cx<double>* x;            // [F][ne][3]
+  cx<double>* r;                  // [F][ne][3] out
+  const double* yacc;             // far-field sums [F][ne][3] complex
+  const FreqDf* fc;
+  const int32_t* flist;
+  int64_t nfl, ne;
+  MatDf m;
+  DfConst C;
+};
+
+__global__ void __launch_bounds__(128) near_df_kernel(const NearDfArgs a) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= a.nfl * a.ne) return;
+  const int64_t f = a.flist[t / a.ne], i = t % a.ne;
+  const FreqDf F = a.fc[f];
+  const MatDf& m = a.m;
+  const DfConst& C = a.C;
+  const cx<double> pf = a.pfac[f];
+  const D4 c = a.cen[i];
+  const df xi0 = df_from(c.x), xi1 = df_from(c.y), xi2 = df_from(c.z);
+  const df z0 = dfm(0.f, 0.f);
+  cdf o[3] = {cmk(z0, z0), cmk(z0, z0), cmk(z0, z0)};
+  // vT = -x or -k, vU = k or x of a source element (FP64), as in the far sweep
+  auto sources = [&](int64_t e, cx<double>* vT, cx<double>* vU) {
+    const cx<double>* xv = a.x + (f * a.ne + e) * 3;
+    const bool dir = a.bc && a.bc[e] == BEM_BC_DISPLACEMENT;
+    for (int q = 0; q < 3; ++q) {
+      const double kv = a.bcv[3 * e + q];
+      const cx<double> kq = mk(pf.r * kv, pf.i * kv);
+      vT[q] = (-1.0) * (dir ? kq : xv[q]);
+      vU[q] = dir ? xv[q] : kq;
+    }
+  };
+  for (int32_t p = a.ptr[i]; p < a.ptr[i + 1]; ++p) {
+    const int64_t e = a.col[p];
+    cx<double> vT[3], vU[3];
+    sources(e, vT, vU);
+    const D4 nn = a.nrm[e];
+    cdf v[7];
+    for (int q = 0; q < 3; ++q) {
+      v[q] = cmk(df_from(vT[q].r), df_from(vT[q].i));
+      v[4 + q] = cmk(df_from(vU[q].r), df_from(vU[q].i));
+    }
+    v[3] = cmk(df_from(nn.x * vT[0].r + nn.y * vT[1].r + nn.z * vT[2].r),
+               df_from(nn.x * vT[0].i + nn.y * vT[1].i + nn.z * vT[2].i));
+    const df n0 = df_from(nn.x), n1 = df_from(nn.y), n2 = df_from(nn.z);
+#pragma unroll 1
+    for (int q = 0; q < 11; ++q) {
+      const bool seven = q < 7;
+      const D4 P = seven ? a.q7[7 * e + q] : a.q4[4 * e + (q - 7)];
+      const df dx = sub(df_from(P.x), xi0), dy = sub(df_from(P.y), xi1), dz = sub(df_from(P.z), xi2);
+      const df r2 = add(add(mul(dx, dx), mul(dy, dy)), mul(dz, dz));
+      const float q0 = rsqrtf(r2.h);
+      const float rh_ = r2.h * q0;
+      const df r = quick2(rh_, (fmaf(-rh_, rh_, r2.h) + r2.l) * (0.5f * q0));
+      const df rinv = add(dfm(q0, 0.f), mulf(addf(neg(mulf(r, q0)), 1.0f), q0));
+      const df inv_r2 = mul(rinv, rinv);
+      const df rx = mul(dx, rinv), ry = mul(dy, rinv), rz = mul(dz, rinv);
+      const df drdn = add(add(mul(rx, n0), mul(ry, n1)), mul(rz, n2));
+      const df w = seven ? df_from(P.w) : neg(df_from(P.w));   // 7-point rule minus 4-point rule
+      const df cw = mul(mul(w, inv_r2), m.inv4pi);
+      const df cu = mul(mul(w, rinv), m.inv4pimu);
+      const df cwd = mul(cw, drdn);
+      const df zr_s = mul(F.a_re, r), zr_p = mul(F.b_re, r);
+      const df ph_s = mul(F.a_im, r), ph_p = mul(F.b_im, r);
+      const df As = df_exp_neg(zr_s, C), Ap = df_exp_neg(zr_p, C);
+      df sn_, cs_;
+      df_sincos(ph_s, C, sn_, cs_);
+      const cdf Es = cmk(mul(As, cs_), neg(mul(As, sn_)));
+      df_sincos(ph_p, C, sn_, cs_);
+      const cdf Ep = cmk(mul(Ap, cs_), neg(mul(Ap, sn_)));
+      cdf oc[3];
+      point_terms(Es, Ep, cmk(zr_s, ph_s), cmk(zr_p, ph_p), inv_r2, F, m, cw, cwd, cu, drdn, rx, ry, rz, n0,
+                  n1, n2, v, oc);
+      for (int k = 0; k < 3; ++k) o[k] = cmk(add_n(o[k].r, oc[k].r), add_n(o[k].i, oc[k].i));
+    }
+  }
+  // own element (FP64 blocks): -(1/2 I + H_ii) x-part through vT, G_ii through vU
+  cx<double> vT[3], vU[3];
+  sources(i, vT, vU);
+  const cx<double>* Hb = a.Tself + (f * a.ne + i) * 9;
+  const cx<double>* Gb = a.Gself + (f * a.ne + i) * 9;
+  const double* ya = a.yacc + (f * a.ne + i) * 6;
+  cx<double>* ro = a.r + (f * a.ne + i) * 3;
+  for (int rr = 0; rr < 3; ++rr) {
+    cx<double> sacc = mk(ya[2 * rr], ya[2 * rr + 1]);
+    for (int cc = 0; cc < 3; ++cc) {
+      cx<double> d = Hb[3 * rr + cc];
+      if (rr == cc) d.r += 0.5;
+      sacc = cfma(d, vT[cc], sacc);
+      sacc = cfma(Gb[3 * rr + cc], vU[cc], sacc);
+    }
+    ro[rr] = mk(sacc.r + df_to(o[rr].r), sacc.i + df_to(o[rr].i));
+  }
+}
+
+// Own-element Duffy sums (the frequency-dependent part of the singular blocks, Sec. 2.1) in
+// float-float: one warp per (frequency, element), lanes over the element's 3 x 13 x 13 Duffy
+// points (SelfPt table), 13 complex sums per warp:
+//   psi = sum w/r (E_s - J),  chi_ab = sum w/r (P - 3J) rh_a rh_b (6),
+//   a_c = sum w/(4 pi r^2) (A + beta^2) rh_c,  b_c = sum w/(4 pi r^2) (q1 - beta^2) rh_c,
+// the same sums the FP64 path forms point by point; the static CPV, the assembly of the 3 x 3
+// blocks and the preconditioner inverse stay in FP64 (self_blocks_kernel).
+struct SelfDfArgs {
+  const SelfPt* pts;     // [ne][3 kDuffyN^2]
+  const FreqDf* fc;      // [F]
+  int64_t ne, F;
+  MatDf m;
+  DfConst C;
+  cx<double>* out;       // [F][ne][13]
+};
+
+__device__ __forceinline__ df warp_sum_df(df v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h = __shfl_xor_sync(0xffffffffu, v.h, o), l = __shfl_xor_sync(0xffffffffu, v.l, o);
+    v = add_n(v, dfm(h, l));
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(128) self_sums_df_kernel(const SelfDfArgs a) {
+  constexpr int NP = 3 * kDuffyN * kDuffyN;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= a.F * a.ne) return;   // whole warps leave together: blockDim is a multiple of 32
+  const int64_t f = w / a.ne, i = w % a.ne;
+  const FreqDf F = a.fc[f];
+  const MatDf& m = a.m;
+  const DfConst& C = a.C;
+  const df z0 = dfm(0.f, 0.f);
+  cdf acc[13];
+#pragma unroll
+  for (int k = 0; k < 13; ++k) acc[k] = cmk(z0, z0);
+  const SelfPt* P = a.pts + i * NP;
+  for (int t = lane; t < NP; t += 32) {
+    const SelfPt q = P[t];
+    const df r = dfm(q.a.x, q.a.y), rh0 = dfm(q.a.z, q.a.w), rh1 = dfm(q.b.x, q.b.y), rh2 = dfm(q.b.z, q.b.w);
+    const df wq = dfm(q.c.x, q.c.y);
+    const float q0 = 1.0f / r.h;
+    const df rinv = add(dfm(q0, 0.f), mulf(addf(neg(mulf(r, q0)), 1.0f), q0));   // 1/r, one Newton step
+    const df inv_r2 = mul(rinv, rinv);
+    const df zr_s = mul(F.a_re, r), zr_p = mul(F.b_re, r);
+    const df ph_s = mul(F.a_im, r), ph_p = mul(F.b_im, r);
+    const df As = df_exp_neg(zr_s, C), Ap = df_exp_neg(zr_p, C);
+    df sn_, cs_;
+    df_sincos(ph_s, C, sn_, cs_);
+    const cdf Es = cmk(mul(As, cs_), neg(mul(As, sn_)));
+    df_sincos(ph_p, C, sn_, cs_);
+    const cdf Ep = cmk(mul(Ap, cs_), neg(mul(Ap, sn_)));
+    const cdf zs = cmk(zr_s, ph_s), zp = cmk(zr_p, ph_p);
+    const cdf gs = cadd(Es, cmul(zs, Es));
+    const cdf gp = cadd(Ep, cmul(zp, Ep));
+    const cdf Pp = csub(Es, cscale(m.beta2, Ep));
+    cdf J;
+    if (zr_s.h * zr_s.h + ph_s.h * ph_s.h < kZSeriesDf2) {
+      J = cmk(m.d[kSeriesDf - 1], z0);
+#pragma unroll 1
+      for (int k = kSeriesDf - 2; k >= 0; --k) J = cadd(cmul(J, zs), cmk(m.d[k], z0));
+    } else {
+      J = cscale(inv_r2, cmul(csub(gp, gs), F.inv_a2));
+    }
+    const cdf Q = csub(cscalef(6.f, J), cmk(scale2(Pp.r, 2.f), scale2(Pp.i, 2.f)));
+    const cdf A = csub(Q, gs);
+    const cdf q1 = csub(Q, cscale(m.c1m2b2, gp));
+    const df cu = mul(wq, rinv);
+    const cdf psi = cscale(cu, csub(Es, J));
+    const cdf chi = cscale(cu, csub(Pp, cscalef(3.f, J)));
+    const df sc = mul(mul(wq, inv_r2), m.inv4pi);
+    const cdf ra = cscale(sc, cmk(add(A.r, m.beta2), A.i));
+    const cdf rb = cscale(sc, cmk(sub(q1.r, m.beta2), q1.i));
+    // running sums stay normalised (add_n); the terms may be lazily normalised
+    auto accum = [](cdf& s, cdf t) { s = cmk(add_n(s.r, t.r), add_n(s.i, t.i)); };
+    accum(acc[0], psi);
+    const df rr[6] = {mul(rh0, rh0), mul(rh0, rh1), mul(rh0, rh2), mul(rh1, rh1), mul(rh1, rh2), mul(rh2, rh2)};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) accum(acc[1 + k], cscale(rr[k], chi));
+    const df rh[3] = {rh0, rh1, rh2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      accum(acc[7 + c], cscale(rh[c], ra));
+      accum(acc[10 + c], cscale(rh[c], rb));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 13; ++k) acc[k] = cmk(warp_sum_df(acc[k].r), warp_sum_df(acc[k].i));
+  if (lane == 0) {
+    cx<double>* o = a.out + w * 13;
+#pragma unroll
+    for (int k = 0; k < 13; ++k) o[k] = mk(df_to(acc[k].r), df_to(acc[k].i));
+  }
+}
+
 size_t resid_df_smem() {
   return sizeof(float) * 12 * kFT * kTB + sizeof(float) * kS * 4 * 8 + sizeof(float) * kS * 8 +
          sizeof(cdf) * kS * kFT * 7 + sizeof(FreqDf) * kFT + sizeof(DfConst);
@@ -256,8 +472,8 @@ DfConst make_df_const() {
 
 }  // namespace
 
-// r[f] = K(s_f) k_f - A(s_f) x[f] for the listed frequencies: far field in float-float, near
-// field and own element in FP64.
+// r[f] = K(s_f) k_f - A(s_f) x[f] for the listed frequencies: far and near field in float-float,
+// the own element's blocks applied in FP64.
 void residual_df(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::vector<int32_t>* flist) {
   BEM_REQUIRE(ctx->bc.set, "residual needs boundary conditions");
   const int64_t nfl = stage_flist(ctx, flist, 0);
@@ -298,8 +514,54 @@ void residual_df(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::ve
     BEM_LAUNCHED();
     ctx->launches++;
   }
-  near_residual64(ctx, x, r, nfl);
+  {
+    NearDfArgs b;
+    b.q4 = ctx->mesh.q4_64.as<D4>();
+    b.q7 = ctx->mesh.q7_64.as<D4>();
+    b.cen = ctx->mesh.c64.as<D4>();
+    b.nrm = ctx->mesh.n64.as<D4>();
+    b.ptr = ctx->mesh.near_ptr.as<int32_t>();
+    b.col = ctx->mesh.near_col.as<int32_t>();
+    b.bc = ctx->bc.d_type.as<int8_t>();
+    b.bcv = ctx->bc.d_value.as<double>();
+    b.pfac = ctx->fs.pfac.as<cx<double>>();
+    b.Tself = ctx->fs.Tself.as<cx<double>>();
+    b.Gself = ctx->fs.Gself.as<cx<double>>();
+    b.x = x;
+    b.r = r;
+    b.yacc = ctx->yacc.as<double>();
+    b.fc = ctx->fs.fcdf.as<FreqDf>();
+    b.flist = ctx->flist_d.as<int32_t>();
+    b.nfl = nfl;
+    b.ne = ctx->mesh.ne;
+    b.m = a.m;
+    b.C = a.C;
+    ProfScope ps(ctx, PK_NEAR64, nfl);
+    near_df_kernel<<<grid_for(nfl * b.ne, 128), 128, 0, ctx->stream>>>(b);
+    BEM_LAUNCHED();
+    ctx->launches++;
+  }
   ctx->f64_applies++;
+}
+
+void self_sums_df(bem_ctx* ctx, cx<double>* out) {
+  const MatC<double> md = mat_constants64(ctx->mat);
+  SelfDfArgs a;
+  a.pts = ctx->mesh.self_pts.as<SelfPt>();
+  a.fc = ctx->fs.fcdf.as<FreqDf>();
+  a.ne = ctx->mesh.ne;
+  a.F = ctx->fs.F;
+  a.m.beta2 = df_split(md.beta2);
+  a.m.c1m2b2 = df_split(md.c1m2b2);
+  a.m.inv4pimu = df_split(md.inv4pimu);
+  a.m.inv4pi = df_split(kInv4Pi);
+  for (int t = 0; t < kSeriesDf; ++t) a.m.d[t] = df_split(md.d[t]);
+  a.C = make_df_const();
+  a.out = out;
+  const int64_t threads = 32 * a.F * a.ne;
+  self_sums_df_kernel<<<grid_for(threads, 128), 128, 0, ctx->stream>>>(a);
+  BEM_LAUNCHED();
+  ctx->launches++;
 }
 
 // FreqDf table for the current frequency set (called by prepare_frequencies)

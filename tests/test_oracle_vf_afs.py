@@ -11,6 +11,7 @@
 import math
 
 import numpy as np
+import pytest
 
 import workloads as W
 from oracle import afs, closed_form as CF, fsm, vf
@@ -93,6 +94,50 @@ def test_afs_on_cavity_closed_form():
     m = W.CAVITY_MATERIAL
     ur = lambda s: np.repeat(CF.cavity_ur(s, 1.0, m.mu, m.nu, m.rho, W.CAVITY_P0)[:, None], 2, axis=1)
     res = afs.run(ur, 250.0, 63 * math.pi / 0.02, 0.02, orf=[0], test=[1], J0=8)
+    ex = CF.cavity_ur_time(res.t, 1.0, m.mu, m.nu, m.rho, W.CAVITY_P0)
+    assert np.abs(res.h[:, 1] - ex).max() < 1e-8 * np.abs(ex).max()
+    assert len(res.s) < 64
+
+
+def test_pick_new_several_frequencies():
+    """The batch variant's selection: the first pick is the paper's s_new (argmax away from
+    samples); further picks mask +-Omega/(2J) around earlier ones and stop below 0.1 of the first."""
+    omega = 1000.0
+    grid = 10.0 + 1j * np.linspace(0.0, omega, 1001)
+    w = grid.imag
+    d = (1.0 * np.exp(-((w - 300) / 20) ** 2) + 0.5 * np.exp(-((w - 700) / 20) ** 2)
+         + 0.3 * np.exp(-((w - 320) / 5) ** 2) + 0.05 * np.exp(-((w - 900) / 20) ** 2))
+    s = 10.0 + 1j * np.array([0.0, 500.0, 1000.0, 300.0])      # a sample sits on the top peak
+    one = afs.pick_new(grid, d, s, omega, batch=1)
+    # the top peak at 300 sits on a sample (skipped within 1.5 spacings): the argmax elsewhere
+    assert len(one) == 1
+    ref = d.copy()
+    ref[np.abs(w[:, None] - s.imag[None, :]).min(axis=1) < 1.5] = -1
+    assert one == [int(np.argmax(ref))]
+    many = afs.pick_new(grid, d, s, omega, batch=4)
+    assert many[0] == one[0]
+    half = omega / (2 * len(s))
+    for a in range(len(many)):
+        assert d[many[a]] >= 0.1 * d[many[0]]
+        for b in range(a):
+            assert abs(w[many[a]] - w[many[b]]) > half
+    assert not any(abs(w[g] - 900) < 50 for g in many)          # below 0.1 of the first pick
+
+
+@pytest.mark.parametrize("batch", [2, 4])
+def test_afs_several_new_frequencies_per_step(batch):
+    poles, R = _rational()
+    T = 0.04
+    eta = 3 * math.log(10) / T
+    res = afs.run(lambda s: vf.evaluate(s, poles, R), eta, 6000.0, T, orf=[0, 1, 2, 3],
+                  test=[4, 5], J0=8, batch=batch)
+    exact = vf.time_response(res.t, poles, R)
+    assert np.abs(res.h - exact).max() < 1e-9 * np.abs(exact).max()
+    assert len(res.s) < 6000.0 * T / math.pi + 1
+    assert len(np.unique(np.round(res.s.imag, 9))) == len(res.s)
+    m = W.CAVITY_MATERIAL
+    ur = lambda s: np.repeat(CF.cavity_ur(s, 1.0, m.mu, m.nu, m.rho, W.CAVITY_P0)[:, None], 2, axis=1)
+    res = afs.run(ur, 250.0, 63 * math.pi / 0.02, 0.02, orf=[0], test=[1], J0=8, batch=batch)
     ex = CF.cavity_ur_time(res.t, 1.0, m.mu, m.nu, m.rho, W.CAVITY_P0)
     assert np.abs(res.h[:, 1] - ex).max() < 1e-8 * np.abs(ex).max()
     assert len(res.s) < 64
