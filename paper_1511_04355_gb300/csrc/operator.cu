@@ -370,6 +370,178 @@ __global__ void BEM_FAR_BOUNDS(TB) far_kernel(const FarArgs<R> a) {
   }
 }
 
+// FP32 far field in apply mode (y = A x or K x), frequency-outer loop: for each source element
+// the geometry of its 4 quadrature points is formed once and kept in registers, then for each of
+// the CTA's frequencies the 4 points are summed.  The terms that multiply the element's source
+// values v and normal n, sum_q t1_q v + sum_q t2_q n (T columns) or sum_q psi_q v (U columns),
+// are accumulated over the points and applied once per element; only the rh_q term stays per
+// point.  REC: equally spaced group, E(s_k) = E(s_{k-1}) e^{-i delta r / c} per point.
+// Same staging, shared-memory layout and accumulation as far_kernel<float, ..., RESID = false>.
+template <int TB, int S, int FT, bool REC>
+__global__ void __launch_bounds__(TB) far32_kernel(const FarArgs<float> a) {
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  float* acc = reinterpret_cast<float*>(smem_raw);                            // [6 FT][TB]
+  float4* sq = reinterpret_cast<float4*>(smem_raw + sizeof(float) * 6 * FT * TB);  // [S][4]
+  float4* sn = sq + 4 * S;                                                     // [S]
+  float4* sql = sn + S;                                                        // [S][4]
+  cx<float>* sv = reinterpret_cast<cx<float>*>(sql + 4 * S);                  // [S][FT][4]
+  FreqC<float>* sfc = reinterpret_cast<FreqC<float>*>(sv + 4 * FT * S);       // [FT]
+
+  const int tid = threadIdx.x;
+  FarGroup grp{};
+  if constexpr (REC) grp = a.groups[blockIdx.y];
+  const int64_t g0 = REC ? (int64_t)grp.start : (int64_t)blockIdx.y * FT;
+  const int nf = REC ? grp.count : (int)min((int64_t)FT, a.nfl - g0);
+  const int64_t src0 = (int64_t)blockIdx.z * a.chunk;
+  const int64_t src1 = min(a.ne, src0 + a.chunk);
+  const int64_t i = (int64_t)blockIdx.x * TB + tid;
+  const bool valid = i < a.ne;
+  float xi0 = 0, xi1 = 0, xi2 = 0;
+  float4 xil = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (valid) {
+    const float4 c = a.cen[i];
+    xi0 = c.x;
+    xi1 = c.y;
+    xi2 = c.z;
+    xil = a.cenlo[i];
+  }
+  if (tid < FT) {
+    if (tid < nf) sfc[tid] = a.fc[a.flist[g0 + tid]];
+    else sfc[tid] = FreqC<float>{};
+  }
+#pragma unroll
+  for (int k = 0; k < 6 * FT; ++k) acc[k * TB + tid] = 0.f;
+  const MatC<float>& m = a.m;
+  __syncthreads();
+  bool same_re = true;
+  for (int k = 1; k < nf; ++k) same_re = same_re && sfc[k].a.r == sfc[0].a.r;
+  const float re_s = -sfc[0].a.r;
+  const float re_p = -(sfc[0].a.r * m.beta);
+  const float inv4pi = (float)kInv4Pi;
+
+  for (int64_t e0 = src0; e0 < src1; e0 += S) {
+    const int ns = (int)min((int64_t)S, src1 - e0);
+    __syncthreads();
+    for (int t = tid; t < 4 * ns; t += TB) sq[t] = a.q4[4 * e0 + t];
+    for (int t = tid; t < 4 * ns; t += TB) sql[t] = a.q4lo[4 * e0 + t];
+    for (int t = tid; t < ns; t += TB) {
+      float4 n = a.nrm[e0 + t];
+      n.w = column_code(a.bc, e0 + t, a.which);
+      sn[t] = n;
+    }
+    for (int t = tid; t < ns * FT; t += TB) {
+      const int e = t / FT, k = t % FT;
+      const int64_t ge = e0 + e;
+      cx<float> v0 = mk(0.f, 0.f), v1 = v0, v2 = v0;
+      if (k < nf) {
+        const cx<float>* xv = a.x + ((int64_t)a.flist[g0 + k] * a.ne + ge) * 3;
+        v0 = xv[0];
+        v1 = xv[1];
+        v2 = xv[2];
+      }
+      const float4 n = a.nrm[ge];
+      cx<float>* o = sv + 4 * (e * FT + k);
+      o[0] = v0;
+      o[1] = v1;
+      o[2] = v2;
+      o[3] = mk(n.x * v0.r + n.y * v1.r + n.z * v2.r, n.x * v0.i + n.y * v1.i + n.z * v2.i);
+    }
+    __syncthreads();
+
+    for (int e = 0; e < ns; ++e) {
+      const float4 nn = sn[e];
+      const bool self = (e0 + e == i);
+      const bool isU = fabsf(nn.w) > 1.5f;
+      const float sign = nn.w > 0 ? 1.f : -1.f;
+      // the element's 4 points: distance, direction, weights, amplitudes (and recurrence state)
+      float r[4], rlo[4], ir2[4], rh0[4], rh1[4], rh2[4], drdn[4], cwu[4], ams[4], amp[4];
+      cx<float> Es[4], Ep[4], ws[4], wp[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 p = sq[4 * e + q];
+        const Dist<float> D = distance(p.x, p.y, p.z, sql[4 * e + q], xi0, xi1, xi2, xil, self);
+        r[q] = D.r;
+        rlo[q] = D.r_lo;
+        ir2[q] = D.rinv * D.rinv;
+        rh0[q] = D.dx * D.rinv;
+        rh1[q] = D.dy * D.rinv;
+        rh2[q] = D.dz * D.rinv;
+        drdn[q] = rh0[q] * nn.x + rh1[q] * nn.y + rh2[q] * nn.z;
+        const float w = self ? 0.f : p.w * sign;
+        cwu[q] = isU ? w * D.rinv * m.inv4pimu : w * ir2[q] * inv4pi;
+        ams[q] = amp[q] = -1.f;
+        if (same_re) {
+          ams[q] = __expf(re_s * r[q]);
+          amp[q] = __expf(re_p * r[q]);
+        }
+        if constexpr (REC) {
+          radial_exps(r[q], sfc[0], m, rlo[q], ams[q], amp[q], Es[q], Ep[q]);
+          ws[q] = step_factor(grp.ws_hi, grp.ws_lo, r[q], rlo[q]);
+          wp[q] = step_factor(grp.wp_hi, grp.wp_lo, r[q], rlo[q]);
+        }
+      }
+#pragma unroll 1
+      for (int k = 0; k < nf; ++k) {
+        const FreqC<float>& F = sfc[k];
+        const cx<float>* v = sv + 4 * (e * FT + k);
+        const cx<float> v0 = v[0], v1 = v[1], v2 = v[2], nv = v[3];
+        cx<float> T1 = mk(0.f, 0.f), T2 = T1, o0 = T1, o1 = T1, o2 = T1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          cx<float> es, ep;
+          if constexpr (REC) {
+            if (k > 0) {
+              Es[q] = Es[q] * ws[q];
+              Ep[q] = Ep[q] * wp[q];
+            }
+            es = Es[q];
+            ep = Ep[q];
+          } else {
+            radial_exps(r[q], F, m, rlo[q], ams[q], amp[q], es, ep);
+          }
+          const Radial<float> K = radial_given(r[q], ir2[q], F, m, es, ep);
+          const cx<float> rv = mk(rh0[q] * v0.r + rh1[q] * v1.r + rh2[q] * v2.r,
+                                  rh0[q] * v0.i + rh1[q] * v1.i + rh2[q] * v2.i);
+          if (!isU) {
+            // T: o_c += cw [A (dr/dn v_c + (rh.v) n_c) + rh_c (q1 (n.v) + q2 dr/dn (rh.v))]
+            const TCoef<float> T = tcoef(K, m);
+            const cx<float> al = cwu[q] * T.A;
+            T1 = axpy(drdn[q], al, T1);
+            T2 = cfma(al, rv, T2);
+            const cx<float> t3 = cwu[q] * cfma(T.q1, nv, drdn[q] * (T.q2 * rv));
+            o0 = axpy(rh0[q], t3, o0);
+            o1 = axpy(rh1[q], t3, o1);
+            o2 = axpy(rh2[q], t3, o2);
+          } else {
+            // U: o_c += cu [(E_s - J) v_c - (P - 3J) rh_c (rh.v)]
+            T1 = T1 + cwu[q] * (K.Es - K.J);
+            const cx<float> crv = (cwu[q] * axpy(-3.f, K.J, K.P)) * rv;
+            o0 = axpy(-rh0[q], crv, o0);
+            o1 = axpy(-rh1[q], crv, o1);
+            o2 = axpy(-rh2[q], crv, o2);
+          }
+        }
+        o0 = cfma(T1, v0, axpy(nn.x, T2, o0));
+        o1 = cfma(T1, v1, axpy(nn.y, T2, o1));
+        o2 = cfma(T1, v2, axpy(nn.z, T2, o2));
+        float* ac = acc + (6 * k) * TB + tid;
+        ac[0] += o0.r;
+        ac[TB] += o0.i;
+        ac[2 * TB] += o1.r;
+        ac[3 * TB] += o1.i;
+        ac[4 * TB] += o2.r;
+        ac[5 * TB] += o2.i;
+      }
+    }
+  }
+  if (!valid) return;
+  for (int k = 0; k < nf; ++k) {
+    double* yo = a.yacc + ((int64_t)a.flist[g0 + k] * a.ne + i) * 6;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) atomicAdd(yo + c, (double)acc[(6 * k + c) * TB + tid]);
+  }
+}
+
 template <class R, int TB, int S, int FT, bool RESID>
 static size_t far_smem() {
   using V = typename V4<R>::T;
@@ -673,11 +845,17 @@ static void launch_far_part(bem_ctx* ctx, const cx<R>* x, int which, int64_t off
   nsplit = (a.ne + chunk - 1) / chunk;
   a.chunk = chunk;
   const size_t smem = far_smem<R, TB, S, FT, RESID>();
-  BEM_CUDA(cudaFuncSetAttribute(far_kernel<R, TB, S, FT, RESID, REC>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const dim3 grid((unsigned)tb, (unsigned)groups, (unsigned)nsplit);
   ProfScope ps(ctx, RESID ? PK_RES64 : (sizeof(R) == 4 ? PK_FAR32 : PK_FAR64), nfl);
-  far_kernel<R, TB, S, FT, RESID, REC><<<grid, TB, smem, ctx->stream>>>(a);
+  if constexpr (sizeof(R) == 4 && !RESID) {
+    BEM_CUDA(cudaFuncSetAttribute(far32_kernel<TB, S, FT, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    far32_kernel<TB, S, FT, REC><<<grid, TB, smem, ctx->stream>>>(a);
+  } else {
+    BEM_CUDA(cudaFuncSetAttribute(far_kernel<R, TB, S, FT, RESID, REC>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    far_kernel<R, TB, S, FT, RESID, REC><<<grid, TB, smem, ctx->stream>>>(a);
+  }
   BEM_LAUNCHED();
   ctx->launches++;
 }
