@@ -408,6 +408,106 @@ def kernel_case():
     print("kernel case done")
 
 
+def workload_uneven():
+    """The uneven-instance workload: 16 ellipsoidal cavities (icosphere levels 2-5, 320-20480
+    triangles, their own materials), 64 frequencies each, solved one context after another and
+    then all together through bem_solve_batch (one host worker and one stream per context)."""
+    import torch
+
+    import paper_1511_04355_gb300 as P
+
+    insts = W.uneven_instances(n_inst=16, levels=(2, 3, 4, 5))
+    s = W.fsm_frequencies(T_WIN, SIGMA, 64)
+    ctxs = []
+    for v, f, mat in insts:
+        c = P.Context(0)
+        c.set_mesh(v, f)
+        c.set_material(mat.mu, mat.nu, mat.rho)
+        c.set_bc(np.zeros(len(f), np.int8), W.pressure_pattern(v, f), P.BEM_PROFILE_STEP)
+        c.set_options(precision=P.BEM_PREC_MIXED, tol=TOL)
+        ctxs.append(c)
+    outs = [np.zeros((len(s), 3 * c.ne), np.complex128) for c in ctxs]
+    # warm-up (allocations, module load)
+    P.bem_solve_batch([(c.h, s[:2], o[:2]) for c, o in zip(ctxs, outs)])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq_info = []
+    for k, (c, o) in enumerate(zip(ctxs, outs)):
+        t1 = time.perf_counter()
+        seq_info.append(c.solve(s, o)[1])
+        info = seq_info[-1]
+        print(json.dumps({"instance": k, "triangles": c.ne, "seconds": time.perf_counter() - t1,
+                          "iterations": int(info["iterations"].sum()),
+                          "max_refinements": int(info["refinements"].max())}), file=sys.stderr, flush=True)
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    res = P.bem_solve_batch([(c.h, s, o) for c, o in zip(ctxs, outs)])
+    t_bat = time.perf_counter() - t0
+    n = len(s) * len(ctxs)
+    ok = all((info["status"] == 0).all() and (info["residual"] <= TOL).all() for _, info in res)
+    line = {"workload": "16 uneven ellipsoidal cavities (icosphere levels 2-5, 320-20480 triangles), "
+                        "64 frequencies each, mixed path to 1e-6",
+            "triangles": [len(f) for _, f, _ in insts], "solves": n,
+            "sequential": {"seconds": t_seq, "solves_per_s": n / t_seq},
+            "batched": {"seconds": t_bat, "solves_per_s": n / t_bat},
+            "speedup_batched_vs_sequential": t_seq / t_bat, "all_certified": bool(ok),
+            "iterations_total": int(sum(int(i["iterations"].sum()) for i in seq_info))}
+    print(json.dumps(line), flush=True)
+
+
+def workload_porous_afs(full=False):
+    """The porous-block workload: a 1 m block with 27 seeded spherical voids (radii 0.08-0.15 m),
+    traction on z = 0, z = 1 fixed; the step response of six unknowns by a 256-frequency FSM and
+    by AFS over the same band, both through the library.  full: the ~30000-triangle recipe
+    (42 x 42 grid per face, level-2 voids); else a reduced mesh (20 x 20 per face, level-1 voids,
+    6960 triangles).  GMRES(200): box problems with a fixed face need hundreds of iterations at
+    the upper frequencies, where GMRES(50) restarts stall."""
+    import paper_1511_04355_gb300 as P
+
+    if full:
+        pb = W.porous_block(n=(42, 42, 42), n_voids=27, void_level=2)
+    else:
+        pb = W.porous_block(n=(20, 20, 20), n_voids=27, void_level=1)
+    v, f, m = pb["verts"], pb["tris"], pb["material"]
+    c = P.Context(0)
+    c.set_mesh(v, f)
+    c.set_material(m.mu, m.nu, m.rho)
+    c.set_bc(pb["bc_type"], pb["bc_value"], P.BEM_PROFILE_STEP)
+    c.set_options(precision=P.BEM_PREC_MIXED, tol=TOL, restart=200, max_iters=4000, max_refine=20)
+    face = pb["face"]
+    cent = v[f].mean(axis=1)
+    def nearest(mask, target):
+        idx = np.flatnonzero(mask)
+        return int(idx[np.argmin(np.linalg.norm(cent[idx] - target, axis=1))])
+    voids = np.flatnonzero(face < 0)
+    dofs = np.array([3 * nearest(face == 4, [0.5, 0.5, 0.0]) + 2,       # loaded face, u_z
+                     3 * nearest(face == 0, [0.0, 0.5, 0.5]) + 0,       # side face, u_x
+                     3 * int(voids[0]) + 2, 3 * int(voids[len(voids) // 2]) + 2,
+                     3 * nearest(face == 4, [0.25, 0.75, 0.0]) + 2,
+                     3 * int(voids[-1]) + 2])
+    period, nc = 2 * T_WIN, 256
+    omega = (nc - 1) * math.pi / T_WIN
+    t = np.linspace(0.0, 0.01, 201)
+    t0 = time.perf_counter()
+    fsm_out, _ = c.fsm(period, SIGMA, nc, t, dofs)
+    t_fsm = time.perf_counter() - t0
+    print(json.dumps({"porous_fsm_seconds": t_fsm, "triangles": len(f)}), file=sys.stderr, flush=True)
+    prm = P.bem_default_afs_params(eta=SIGMA, omega_max=omega, T=period, J0=8, max_samples=200)
+    t0 = time.perf_counter()
+    afs_out, info = c.afs(prm, dofs[:4], dofs[4:], t)
+    t_afs = time.perf_counter() - t0
+    late = t > 2e-3
+    rel = np.sqrt(np.sum((afs_out[late] - fsm_out[late]) ** 2, axis=0) / np.sum(fsm_out[late] ** 2, axis=0))
+    line = {"workload": f"porous block 1x1x1 m, 27 voids, {len(f)} triangles ({3 * len(f)} unknowns), "
+                        f"step traction on z=0, z=1 fixed; band {omega:.0f} rad/s",
+            "fsm": {"n_c": nc, "seconds": t_fsm},
+            "afs": {"n_c": int(info["n_samples"]), "seconds": t_afs, "poles": len(info["poles"]),
+                    "E1": float(info["E1"][-1]), "E2": float(info["E2"][-1]),
+                    "seconds_solve": info["seconds_solve"], "seconds_fit": info["seconds_fit"]},
+            "afs_vs_fsm_rel_l2_after_2ms": rel.tolist()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -417,9 +517,17 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the small operator/residual case used for ncu captures")
+    ap.add_argument("--workload", choices=["uneven", "porous-afs", "porous-afs-full"],
+                    help="run one of the other workloads instead of the benchmark (own JSON line)")
     args = ap.parse_args()
     if args.kernel_case:
         kernel_case()
+        return
+    if args.workload == "uneven":
+        workload_uneven()
+        return
+    if args.workload in ("porous-afs", "porous-afs-full"):
+        workload_porous_afs(full=args.workload == "porous-afs-full")
         return
     if args.warmup < 3:
         args.warmup = 3

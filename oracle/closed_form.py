@@ -1,4 +1,6 @@
-"""Closed-form pressurised spherical cavity in a full space (pin for the oracle; FP64).
+"""Closed-form solutions used as pins for the oracle (FP64, test infrastructure only).
+
+1. Pressurised spherical cavity in a full space.
 
 Radially symmetric field outside a cavity of radius a in an unbounded isotropic solid, driven
 by a pressure P(s) on the wall (Laplace domain, Re s > 0).  With the outgoing potential
@@ -6,6 +8,15 @@ phi = A e^{-s r / c_p} / r, u_r = d phi / dr and the wall condition sigma_rr(a) 
     u_r(a, s) = P(s) a (1 + s a / c_p) / (rho s^2 a^2 + 4 mu (1 + s a / c_p)).
 For a step pressure P(s) = p0 / s this is rational in s with poles at 0 and at the roots of
 rho a^2 c_p s^2 + 4 mu a s + 4 mu c_p = 0, so the time response follows from residues.
+
+2. Prismatic rod with Poisson's ratio 0 (the rod of Sec. 4, Example 1): fixed at x = 0, axial
+traction P(s) = P0 / s on the end x = L, lateral faces free.  With nu = 0 the 1-D bar field
+u = u(x, t) e_x is an exact solution of the 3-D equations (no lateral coupling), with
+c = sqrt(E / rho).  Laplace domain: u(x, s) = A sinh(s x / c) with E u_x(L) = P0 / s, so
+    u(L, s) = P0 c tanh(s L / c) / (E s^2).
+Expanding tanh z = 1 + 2 sum_{n>=1} (-1)^n e^{-2 n z} and inverting term by term:
+    u(L, t) = (P0 c / E) [t + 2 sum_{n>=1} (-1)^n (t - 2 n L / c) H(t - 2 n L / c)],
+a triangle wave between 0 and 2 P0 L / E of period 4 L / c.
 """
 from __future__ import annotations
 
@@ -39,3 +50,22 @@ def cavity_ur_time(t, a, mu, nu, rho, p0):
     poles, res = cavity_poles_residues(a, mu, nu, rho, p0)
     t = np.asarray(t, dtype=np.float64)
     return np.real(np.sum(res[:, None] * np.exp(poles[:, None] * t[None, :]), axis=0))
+
+
+def rod_end_displacement_s(s, L, E, rho, P0):
+    """u(L, s) of the nu = 0 rod (Laplace domain)."""
+    c = np.sqrt(E / rho)
+    s = np.asarray(s, dtype=np.complex128)
+    return P0 * c * np.tanh(s * L / c) / (E * s * s)
+
+
+def rod_end_displacement_t(t, L, E, rho, P0):
+    """u(L, t) of the nu = 0 rod (time domain, the reflection series)."""
+    c = np.sqrt(E / rho)
+    t = np.asarray(t, dtype=np.float64)
+    u = t.copy()
+    n_max = int(np.ceil(t.max() * c / (2 * L))) + 1 if t.size else 0
+    for n in range(1, n_max + 1):
+        tn = t - 2 * n * L / c
+        u += 2 * (-1) ** n * np.where(tn > 0, tn, 0.0)
+    return P0 * c / E * u

@@ -262,6 +262,8 @@ struct bem_ctx {
   bem::DevBuf groups_d;         // FarGroup per CTA frequency group of the current far launches
   std::vector<bem::FarGroup> groups_h;
   int64_t rec_entries = 0;      // leading list entries in equally spaced runs (FP32 recurrence)
+  bem::DevBuf zero_pfac;        // zero profile factors: the residual sweep as an operator
+  bool fp64_op_df = false;      // FP64 GMRES applies the float-float operator (mixed fallback)
   bem::DevBuf yacc;             // FP64 far-field accumulator [F][ne][3] complex
   int64_t launches = 0;         // kernels launched (accumulated, reset per call)
   int64_t f32_applies = 0, f64_applies = 0;
@@ -298,7 +300,10 @@ void apply_operator32(bem_ctx* ctx, const cx<float>* x, cx<float>* y, int which,
 // r[f] = K(s_f) k_f - A(s_f) x[f] in FP64 in one sweep (k = profile(s) * known data)
 void residual64(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::vector<int32_t>* flist);
 // the same with the far field in float-float arithmetic on the FP32 pipes (resid_df.cu)
-void residual_df(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::vector<int32_t>* flist);
+void residual_df(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::vector<int32_t>* flist,
+                 const cx<double>* pfac_override = nullptr);
+// y = A(s) x with the float-float sweeps (FP64-class, ~1e-10 relative) for the listed frequencies
+void apply_operator_df(bem_ctx* ctx, const cx<double>* x, cx<double>* y, const std::vector<int32_t>* flist);
 void build_freq_df(bem_ctx* ctx, const double* s, int64_t F);
 // own-element Duffy sums in float-float: out[F][ne][13] = (psi, chi rh rh (6), T remainder a (3),
 // b (3)) per frequency and element (resid_df.cu)

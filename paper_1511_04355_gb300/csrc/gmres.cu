@@ -321,7 +321,8 @@ struct Ops<float> {
 template <>
 struct Ops<double> {
   static void op(bem_ctx* c, const cx<double>* x, cx<double>* y, const std::vector<int32_t>* l) {
-    apply_operator64(c, x, y, BEM_APPLY_A, l);
+    if (c->fp64_op_df) apply_operator_df(c, x, y, l);
+    else apply_operator64(c, x, y, BEM_APPLY_A, l);
   }
   static void pre(bem_ctx* c, const cx<double>* x, cx<double>* y, const int32_t* a) {
     apply_precond64(c, x, y, a);
@@ -560,7 +561,8 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
       if (rlist.empty()) break;
       // restart from the true residual
       BEM_CUDA(cudaMemcpyAsync(W.part.p, part.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, st));
-      residual64(ctx, x_dev, W.r.as<cx<double>>(), &rlist);
+      if (ctx->fp64_op_df) residual_df(ctx, x_dev, W.r.as<cx<double>>(), &rlist);
+      else residual64(ctx, x_dev, W.r.as<cx<double>>(), &rlist);
       norm2_kernel<double><<<(unsigned)F, 256, 0, st>>>(W.r.as<cx<double>>(), N, W.part.as<int32_t>(),
                                                         W.rn2.as<double>());
       ctx->launches++;
@@ -688,6 +690,13 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
     BEM_CUDA(cudaStreamSynchronize(st));
   }
   reserve_inner<double>(W.V64, W.z64, W.w64, F, N, m);
+  // the fallback's operator: float-float (FP64-class to ~1e-10, several times faster than the
+  // FP64 unit) when the tolerance leaves room for that, native FP64 below 1e-8
+  struct DfOpScope {
+    bem_ctx* c;
+    DfOpScope(bem_ctx* c_, bool on) : c(c_) { c->fp64_op_df = on; }
+    ~DfOpScope() { c->fp64_op_df = false; }
+  } df_scope(ctx, o.tol >= 1e-8);
   fp64_loop(W.V64, W.z64, W.w64);
   // certify with the true FP64 residual
   {

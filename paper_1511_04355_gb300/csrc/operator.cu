@@ -136,8 +136,8 @@ __device__ __forceinline__ void u_contract(const Radial<R>& K, R cu, R rh0, R rh
   o[2] = cfma(psi, v2, axpy(-rh2, crv, o[2]));
 }
 
-// Far-field kernel.  Apply mode (RESID = false): y = Op x with Op = A or K, one kernel (T or U)
-// per source column.  Residual mode (RESID = true): y = K k - A x with k = profile(s) * known
+// Far-field kernel (FP64: the plain-FP64 path and the native FP64 residual).  Apply mode
+// (RESID = false): y = Op x with Op = A or K, one kernel (T or U) per source column.  Residual mode (RESID = true): y = K k - A x with k = profile(s) * known
 // data; every source contributes through both kernels, T applied to vT and U to vU where
 // (vT, vU) = (-x_e, k_e) for traction-given and (-k_e, x_e) for displacement-given columns.
 // e^{-i theta} with theta = (w_hi + w_lo)(r + r_lo), |theta| <= 1.5 (the host admits a group
@@ -164,50 +164,33 @@ __device__ __forceinline__ cx<float> step_factor(float w_hi, float w_lo, float r
   return mk(fmaf(-sn, tl, c), -fmaf(c, tl, sn));
 }
 
-// BEM_FAR_MIN_BLOCKS (optional, build flag): compile the far kernels for that many resident CTAs
-// per SM (a register cap); unset, the compiler chooses.
-#ifdef BEM_FAR_MIN_BLOCKS
-#define BEM_FAR_BOUNDS(TB) __launch_bounds__(TB, BEM_FAR_MIN_BLOCKS)
-#else
-#define BEM_FAR_BOUNDS(TB) __launch_bounds__(TB)
-#endif
-
-template <class R, int TB, int S, int FT, bool RESID, bool REC>
-__global__ void BEM_FAR_BOUNDS(TB) far_kernel(const FarArgs<R> a) {
+template <class R, int TB, int S, int FT, bool RESID>
+__global__ void __launch_bounds__(TB) far_kernel(const FarArgs<R> a) {
   using V = typename V4<R>::T;
   constexpr int NV = RESID ? 7 : 4;                                    // cx per (source, freq)
-  constexpr bool FF = sizeof(R) == 4;                                  // float-float distances
-  constexpr int NL = FF ? 4 * S : 0;
   extern __shared__ __align__(32) unsigned char smem_raw[];
   // accumulators: per-tile partial sums (registers) are added into R-precision sums here, then
   // into the FP64 result with one atomic add per output at the end
   R* acc = reinterpret_cast<R*>(smem_raw);                            // [6 FT][TB]
   V* sq = reinterpret_cast<V*>(smem_raw + sizeof(R) * 6 * FT * TB);   // [S][4]
   V* sn = sq + 4 * S;                                                  // [S]
-  float4* sql = reinterpret_cast<float4*>(sn + S);                    // [S][4] low parts (FP32)
-  cx<R>* sv = reinterpret_cast<cx<R>*>(sql + NL);                     // [S][FT][NV]
+  cx<R>* sv = reinterpret_cast<cx<R>*>(sn + S);                       // [S][FT][NV]
   FreqC<R>* sfc = reinterpret_cast<FreqC<R>*>(sv + NV * FT * S);      // [FT]
 
   const int tid = threadIdx.x;
-  // the CTA's frequencies: FT consecutive list entries per blockIdx.y, or (recurrence kernel) the
-  // run its group descriptor names
-  FarGroup grp{};
-  if constexpr (REC) grp = a.groups[blockIdx.y];
-  const int64_t g0 = REC ? (int64_t)grp.start : (int64_t)blockIdx.y * FT;
-  const int nf = REC ? grp.count : (int)min((int64_t)FT, a.nfl - g0);
+  const int64_t g0 = (int64_t)blockIdx.y * FT;   // position in the frequency list
+  const int nf = (int)min((int64_t)FT, a.nfl - g0);
   const unsigned mask = (1u << nf) - 1u;
   const int64_t src0 = (int64_t)blockIdx.z * a.chunk;
   const int64_t src1 = min(a.ne, src0 + a.chunk);
   const int64_t i = (int64_t)blockIdx.x * TB + tid;
   const bool valid = i < a.ne;
   R xi0 = 0, xi1 = 0, xi2 = 0;
-  float4 xil = make_float4(0.f, 0.f, 0.f, 0.f);
   if (valid) {
     const V c = a.cen[i];
     xi0 = c.x;
     xi1 = c.y;
     xi2 = c.z;
-    if (FF) xil = a.cenlo[i];
   }
   if (tid < FT) {
     if (tid < nf) sfc[tid] = a.fc[a.flist[g0 + tid]];
@@ -217,22 +200,12 @@ __global__ void BEM_FAR_BOUNDS(TB) far_kernel(const FarArgs<R> a) {
   for (int k = 0; k < 6 * FT; ++k) acc[k * TB + tid] = R(0);
   const MatC<R>& m = a.m;
   __syncthreads();
-  // FP32: when the group's frequencies share Re s, the amplitudes e^{-Re(s) r / c} are formed
-  // once per source point instead of once per frequency
-  bool same_re = FF;
-  for (int k = 1; k < nf; ++k) same_re = same_re && (float)sfc[k].a.r == (float)sfc[0].a.r;
-  const float re_s = FF ? -(float)sfc[0].a.r : 0.f;
-  const float re_p = FF ? -(float)(sfc[0].a.r * m.beta) : 0.f;
-  // equally spaced group (FP32): E(s_j) = E(s_{j-1}) e^{-i delta r / c}, one complex product
-  // per exponential instead of a range reduction and a sine/cosine
   const R inv4pi = R(kInv4Pi);
 
   for (int64_t e0 = src0; e0 < src1; e0 += S) {
     const int ns = (int)min((int64_t)S, src1 - e0);
     __syncthreads();
     for (int t = tid; t < 4 * ns; t += TB) sq[t] = a.q4[4 * e0 + t];
-    if (FF)
-      for (int t = tid; t < 4 * ns; t += TB) sql[t] = a.q4lo[4 * e0 + t];
     for (int t = tid; t < ns; t += TB) {
       V n = a.nrm[e0 + t];
       n.w = (R)column_code(a.bc, e0 + t, a.which);
@@ -285,52 +258,26 @@ __global__ void BEM_FAR_BOUNDS(TB) far_kernel(const FarArgs<R> a) {
     for (int e = 0; e < ns; ++e) {
       const V nn = sn[e];
       const bool self = (e0 + e == i);
-      const bool isU = fabs((float)nn.w) > 1.5f;
+      const bool isU = fabs((double)nn.w) > 1.5;
       const R sign = RESID ? R(1) : (nn.w > 0 ? R(1) : R(-1));
 #pragma unroll 1
       for (int q = 0; q < 4; ++q) {
         const V p = sq[4 * e + q];
-        const Dist<R> D = distance(p.x, p.y, p.z, FF ? sql[4 * e + q] : make_float4(0.f, 0.f, 0.f, 0.f),
-                                   xi0, xi1, xi2, xil, self);
-        const R r = D.r, rinv = D.rinv, r_lo = D.r_lo;
+        const Dist<R> D = distance(p.x, p.y, p.z, make_float4(0.f, 0.f, 0.f, 0.f), xi0, xi1, xi2,
+                                   make_float4(0.f, 0.f, 0.f, 0.f), self);
+        const R r = D.r, rinv = D.rinv;
         const R inv_r2 = rinv * rinv;
         const R rh0 = D.dx * rinv, rh1 = D.dy * rinv, rh2 = D.dz * rinv;
         const R w = self ? R(0) : p.w * sign;
         const R drdn = rh0 * nn.x + rh1 * nn.y + rh2 * nn.z;
         const R cw = w * inv_r2 * inv4pi;
         const R cu = w * rinv * m.inv4pimu;
-        float amp_s = -1.f, amp_p = -1.f;
-        if (same_re) {
-          amp_s = __expf(re_s * (float)r);
-          amp_p = __expf(re_p * (float)r);
-        }
-        cx<R> ws = mk(R(1), R(0)), wp = ws, Es = ws, Ep = ws;
-        if constexpr (REC) {  // one-step factors e^{-i delta r / c_s}, e^{-i beta delta r / c_s}
-          ws = step_factor(grp.ws_hi, grp.ws_lo, (float)r, (float)r_lo);
-          wp = step_factor(grp.wp_hi, grp.wp_lo, (float)r, (float)r_lo);
-        }
-        // E_s, E_p of group member k: in an equally spaced group by the one-step product from
-        // member k - 1, else directly
-        auto exps = [&](int k) {
-          if (REC && k > 0) {
-            Es = Es * ws;
-            Ep = Ep * wp;
-          } else {
-            radial_exps(r, sfc[k], m, r_lo, amp_s, amp_p, Es, Ep);
-          }
-        };
         if (RESID || !isU) {
 #pragma unroll
           for (int k = 0; k < FT; ++k) {
             if (!((mask >> k) & 1u)) continue;
             const cx<R>* v = sv + NV * (e * FT + k);
-            Radial<R> K;
-            if constexpr (REC) {
-              exps(k);
-              K = radial_given(r, inv_r2, sfc[k], m, Es, Ep);
-            } else {
-              K = radial(r, inv_r2, sfc[k], m, r_lo, amp_s, amp_p);
-            }
+            const Radial<R> K = radial(r, inv_r2, sfc[k], m);
             const TCoef<R> T = tcoef(K, m);
             t_contract(T, cw, drdn, rh0, rh1, rh2, nn.x, nn.y, nn.z, v[0], v[1], v[2], v[3], part[k]);
             if (RESID) u_contract(K, cu, rh0, rh1, rh2, v[4], v[5], v[6], part[k]);
@@ -340,13 +287,7 @@ __global__ void BEM_FAR_BOUNDS(TB) far_kernel(const FarArgs<R> a) {
           for (int k = 0; k < FT; ++k) {
             if (!((mask >> k) & 1u)) continue;
             const cx<R>* v = sv + NV * (e * FT + k);
-            Radial<R> K;
-            if constexpr (REC) {
-              exps(k);
-              K = radial_given(r, inv_r2, sfc[k], m, Es, Ep);
-            } else {
-              K = radial(r, inv_r2, sfc[k], m, r_lo, amp_s, amp_p);
-            }
+            const Radial<R> K = radial(r, inv_r2, sfc[k], m);
             u_contract(K, cu, rh0, rh1, rh2, v[0], v[1], v[2], part[k]);
           }
         }
@@ -376,7 +317,8 @@ __global__ void BEM_FAR_BOUNDS(TB) far_kernel(const FarArgs<R> a) {
 // values v and normal n, sum_q t1_q v + sum_q t2_q n (T columns) or sum_q psi_q v (U columns),
 // are accumulated over the points and applied once per element; only the rh_q term stays per
 // point.  REC: equally spaced group, E(s_k) = E(s_{k-1}) e^{-i delta r / c} per point.
-// Same staging, shared-memory layout and accumulation as far_kernel<float, ..., RESID = false>.
+// Shared memory: the accumulators, the source tile (points, low parts, normals, values) and the
+// frequency constants (far_smem<float, ..., RESID = false>).
 template <int TB, int S, int FT, bool REC>
 __global__ void __launch_bounds__(TB) far32_kernel(const FarArgs<float> a) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
@@ -852,9 +794,9 @@ static void launch_far_part(bem_ctx* ctx, const cx<R>* x, int which, int64_t off
                                   (int)smem));
     far32_kernel<TB, S, FT, REC><<<grid, TB, smem, ctx->stream>>>(a);
   } else {
-    BEM_CUDA(cudaFuncSetAttribute(far_kernel<R, TB, S, FT, RESID, REC>,
+    BEM_CUDA(cudaFuncSetAttribute(far_kernel<R, TB, S, FT, RESID>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    far_kernel<R, TB, S, FT, RESID, REC><<<grid, TB, smem, ctx->stream>>>(a);
+    far_kernel<R, TB, S, FT, RESID><<<grid, TB, smem, ctx->stream>>>(a);
   }
   BEM_LAUNCHED();
   ctx->launches++;

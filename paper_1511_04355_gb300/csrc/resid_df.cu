@@ -474,7 +474,8 @@ DfConst make_df_const() {
 
 // r[f] = K(s_f) k_f - A(s_f) x[f] for the listed frequencies: far and near field in float-float,
 // the own element's blocks applied in FP64.
-void residual_df(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::vector<int32_t>* flist) {
+void residual_df(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::vector<int32_t>* flist,
+                 const cx<double>* pfac_override) {
   BEM_REQUIRE(ctx->bc.set, "residual needs boundary conditions");
   const int64_t nfl = stage_flist(ctx, flist, 0);
   if (!nfl) return;
@@ -485,7 +486,7 @@ void residual_df(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::ve
   a.nrm = ctx->mesh.n64.as<D4>();
   a.bc = ctx->bc.d_type.as<int8_t>();
   a.bcv = ctx->bc.d_value.as<double>();
-  a.pfac = ctx->fs.pfac.as<cx<double>>();
+  a.pfac = pfac_override ? pfac_override : ctx->fs.pfac.as<cx<double>>();
   a.x = x;
   a.yacc = ctx->yacc.as<double>();
   a.fc = ctx->fs.fcdf.as<FreqDf>();
@@ -524,7 +525,7 @@ void residual_df(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::ve
     b.col = ctx->mesh.near_col.as<int32_t>();
     b.bc = ctx->bc.d_type.as<int8_t>();
     b.bcv = ctx->bc.d_value.as<double>();
-    b.pfac = ctx->fs.pfac.as<cx<double>>();
+    b.pfac = a.pfac;
     b.Tself = ctx->fs.Tself.as<cx<double>>();
     b.Gself = ctx->fs.Gself.as<cx<double>>();
     b.x = x;
@@ -562,6 +563,28 @@ void self_sums_df(bem_ctx* ctx, cx<double>* out) {
   self_sums_df_kernel<<<grid_for(threads, 128), 128, 0, ctx->stream>>>(a);
   BEM_LAUNCHED();
   ctx->launches++;
+}
+
+// y = A(s) x in float-float for the listed frequencies: the residual sweep with the known data
+// switched off gives r = -A x, negated in place.
+__global__ void negate_rows_kernel(cx<double>* y, const int32_t* flist, int64_t nfl, int64_t n) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nfl * n) return;
+  cx<double>& v = y[(int64_t)flist[t / n] * n + t % n];
+  v = mk(-v.r, -v.i);
+}
+
+void apply_operator_df(bem_ctx* ctx, const cx<double>* x, cx<double>* y, const std::vector<int32_t>* flist) {
+  const int64_t F = ctx->fs.F;
+  ctx->zero_pfac.reserve(sizeof(cx<double>) * F);
+  BEM_CUDA(cudaMemsetAsync(ctx->zero_pfac.p, 0, sizeof(cx<double>) * F, ctx->stream));
+  residual_df(ctx, x, y, flist, ctx->zero_pfac.as<cx<double>>());
+  const int64_t nfl = (int64_t)ctx->flist_h.size(), n = 3 * ctx->mesh.ne;
+  if (nfl) {
+    negate_rows_kernel<<<grid_for(nfl * n, 256), 256, 0, ctx->stream>>>(y, ctx->flist_d.as<int32_t>(), nfl, n);
+    BEM_LAUNCHED();
+    ctx->launches++;
+  }
 }
 
 // FreqDf table for the current frequency set (called by prepare_frequencies)

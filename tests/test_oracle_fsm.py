@@ -91,3 +91,31 @@ def test_cavity_closed_form_poles():
     im = math.sqrt(4.0 * m.mu * m.rho - 4.0 * m.mu ** 2 / cp ** 2) / m.rho
     assert abs(poles[0] - complex(re, -im)) < 1e-6 and abs(poles[2] - complex(re, im)) < 1e-6
     assert abs(res[1] - W.CAVITY_P0 / (4 * m.mu)) < 1e-18
+
+
+def test_rod_closed_form_laplace_and_time_agree():
+    """The nu = 0 rod: the Laplace-domain end displacement P0 c tanh(sL/c)/(E s^2), inverted by
+    the FSM on the rod example's grid (kappa = 3, Hanning, N_c = 110 over T = 0.0155 s), matches
+    the reflection-series time response away from its kinks; the series is a triangle wave of
+    period 4L/c between 0 and 2 P0 L / E."""
+    import numpy as np
+    from oracle import closed_form as CF, fsm
+    L, E, rho, P0, T = 3.0, 2.11e11, 7.85e3, -1e6, 0.0155
+    c = np.sqrt(E / rho)
+    t = np.linspace(0.0, T * 0.6, 400)
+    u = CF.rod_end_displacement_t(t, L, E, rho, P0)
+    ext = CF.rod_end_displacement_t(np.array([0.0, 2 * L / c, 4 * L / c, 6 * L / c]), L, E, rho, P0)
+    assert np.allclose(ext, [0.0, 2 * P0 * L / E, 0.0, 2 * P0 * L / E], atol=1e-12 * abs(P0 * L / E))
+    assert u.min() >= 2 * P0 * L / E * (1 + 1e-12) and u.max() <= 1e-18
+    tp = 4 * L / c
+    assert np.allclose(CF.rod_end_displacement_t(t[t < T * 0.6 - tp] + tp, L, E, rho, P0),
+                       u[t < T * 0.6 - tp], atol=1e-18)
+    eta = fsm.eta_from_kappa(3.0, T)
+    s = fsm.frequencies(eta, T, 218)
+    h = CF.rod_end_displacement_s(s, L, E, rho, P0)
+    inv = fsm.invert(h, eta, T, t, window=True)
+    # away from the kinks (every 2L/c) the windowed inversion follows the triangle wave
+    kink = 2 * L / c
+    far = np.abs(((t + kink / 2) % kink) - kink / 2) > 0.15 * kink
+    err = np.abs(inv - u)[far].max() / np.abs(u).max()
+    assert err < 0.05, err

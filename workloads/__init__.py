@@ -264,3 +264,24 @@ def porous_block(L=(1.0, 1.0, 1.0), n=(8, 8, 8), n_voids=27, radii=(0.08, 0.15),
     bc_type[face == 5] = 1                 # z = Lz fixed (zero displacement)
     return dict(verts=verts, tris=tris, face=face, material=material, bc_type=bc_type,
                 bc_value=bc_value, centres=np.array(centres), radii=np.array(rad))
+
+
+# ----------------------------------------------------------------------------------------------
+# prismatic rod
+# ----------------------------------------------------------------------------------------------
+ROD_MATERIAL = Material(mu=2.11e11 / 2.0, nu=0.0, rho=7.85e3)   # E = 2.11e11 Pa, nu = 0
+ROD_P0 = -1e6                                                   # axial step traction [Pa]
+
+
+def prismatic_rod(L=(3.0, 1.0, 1.0), n=(24, 8, 8), p0=ROD_P0, material=ROD_MATERIAL):
+    """The prismatic rod (box [0,Lx]x[0,Ly]x[0,Lz]) fixed at x = 0, axial step traction p0 e_x on
+    x = Lx, lateral faces free; each face split into the squares of the grid n, two triangles
+    each, normals out of the rod.  Returns (verts, tris, face, material, bc_type, bc_value)."""
+    verts, tris, face = box_surface(L, n)
+    ne = len(tris)
+    bc_type = np.zeros(ne, dtype=np.int8)
+    bc_value = np.zeros((ne, 3))
+    bc_type[face == 0] = 1                    # x = 0 fixed (zero displacement)
+    bc_value[face == 1, 0] = p0               # x = Lx: traction p0 e_x
+    return dict(verts=verts, tris=tris, face=face, material=material, bc_type=bc_type,
+                bc_value=bc_value)
