@@ -119,3 +119,27 @@ def test_rod_closed_form_laplace_and_time_agree():
     far = np.abs(((t + kink / 2) % kink) - kink / 2) > 0.15 * kink
     err = np.abs(inv - u)[far].max() / np.abs(u).max()
     assert err < 0.05, err
+
+
+def test_fsm_grid_matches_the_rod_example_printed_values():
+    """Sec. 4, Example 1 prints, for T = 0.0155 s: dt = pi / Omega_s = 7.11e-5 s,
+    N_s = ceil(T / dt) = 218 and N_c = 110 (tests/golden/rod_example1_fsm_grid.txt).  The oracle's
+    grid s_k = eta + i k 2 pi / T, k = 0 .. N_s/2, reproduces them: N_c = N_s/2 + 1 and
+    Omega_s = (N_c - 1) 2 pi / T with pi / Omega_s = dt to the printed digits."""
+    import math
+    import os
+    import numpy as np
+    from oracle import fsm
+    vals = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "rod_example1_fsm_grid.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    T, Ns = vals["T_s"], int(vals["N_s"])
+    s = fsm.frequencies(fsm.eta_from_kappa(vals["kappa"], T), T, Ns)
+    assert len(s) == int(vals["N_c"])
+    omega = s[-1].imag
+    assert abs(math.pi / omega - vals["dt_s"]) < 0.005e-5
+    assert round(T / (math.pi / omega)) == Ns                    # N_s = T / dt on this grid
+    assert np.allclose(np.diff(s.imag), 2 * math.pi / T)
