@@ -61,3 +61,24 @@ def test_calls_without_gpu_return_error_codes():
     items = (P.bem_batch_item * 2)()
     assert lib.bem_solve_batch(items, 2, 0) == P.BEM_ERR_INVALID_ARG       # null contexts
     assert lib.bem_solve_batch(items, 0, 0) == P.BEM_ERR_INVALID_ARG
+
+
+def test_afs_defaults_are_the_papers_printed_values():
+    """bem_default_afs_params and the oracle's AFS defaults carry the parameters the paper prints
+    (tests/golden/afs_parameters.txt)."""
+    import inspect
+    import os
+    import paper_1511_04355_gb300 as P
+    from oracle import afs as OA
+    vals = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "afs_parameters.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    p = P.bem_default_afs_params()
+    for k in ("J0", "alpha_H", "alpha_L", "E1bar", "E2bar", "Jc"):
+        assert getattr(p, k) == vals[k], k
+    d = {n: v.default for n, v in inspect.signature(OA.run).parameters.items()}
+    for k in ("J0", "alpha_H", "alpha_L", "E1bar", "E2bar", "Jc"):
+        assert d[k] == vals[k], k
