@@ -136,3 +136,59 @@ def test_duffy_integrates_inverse_distance():
     p = np.linalg.norm((a - x0) - t1 * t)
     exact = p * (math.asinh(t2 / p) - math.asinh(t1 / p))
     assert abs(approx - exact) < 1e-12 * exact
+
+
+def _subdivide(p, levels):
+    """4^levels congruent sub-triangles of the triangle p (3, 3) by edge midpoints."""
+    tris = [p]
+    for _ in range(levels):
+        new = []
+        for t in tris:
+            a, b, c = t
+            ab, bc, ca = (a + b) / 2, (b + c) / 2, (c + a) / 2
+            new += [np.array([a, ab, ca]), np.array([ab, b, bc]), np.array([ca, bc, c]), np.array([ab, bc, ca])]
+        tris = new
+    return np.array(tris)
+
+
+def _subdivided_blocks(xi, tri, normal, s, mat, levels, rule=Q.rule_7pt):
+    subs = _subdivide(tri, levels)
+    b, w = rule()
+    pts = np.einsum("qk,ekd->eqd", b, subs).reshape(-1, 3)
+    area = 0.5 * np.linalg.norm(np.cross(subs[:, 1] - subs[:, 0], subs[:, 2] - subs[:, 0]), axis=1)
+    wts = (w[None, :] * area[:, None]).reshape(-1)
+    d = pts - xi
+    T = K.fundamental_T(d, np.broadcast_to(normal, d.shape), s, mat.mu, mat.nu, mat.rho)
+    U = K.fundamental_U(d, s, mat.mu, mat.nu, mat.rho)
+    return np.einsum("q,qij->ij", wts, T), np.einsum("q,qij->ij", wts, U)
+
+
+def test_element_integrals_against_subdivided_quadrature():
+    """Brute force on the 80-triangle sphere: every off-diagonal block H_0e, G_0e of the oracle
+    against the 7-point rule on 4^5 sub-triangles (itself converged: 4^4 agrees to 1e-7).
+    Far sources (4-point rule, |x_0 - c_e| >= 2 h_e): within 3e-3.  Near sources (7-point
+    rule): within 5e-3 from one element size away, within 0.15 for edge neighbours (the rule's
+    near-singular limit), and always closer to the reference than the 4-point rule would be."""
+    import workloads as W
+    from oracle import bem as OB
+    mat = W.CAVITY_MATERIAL
+    v, f = W.icosphere(1, 1.0)
+    g = OB.geometry(v, f)
+    s = 250.0 + 2000.0j
+    H, G = OB.element_blocks(g, s, mat, rows=[0])
+    near = OB.near_mask(g)[0]
+    dist = np.linalg.norm(g.centroid - g.centroid[0], axis=1) / g.h
+    for e in range(1, len(f)):
+        x0 = g.centroid[0]
+        h5, g5 = _subdivided_blocks(x0, g.p[e], g.normal[e], s, mat, 5)
+        h4, g4 = _subdivided_blocks(x0, g.p[e], g.normal[e], s, mat, 4)
+        assert np.abs(h5 - h4).max() <= 1e-7 * np.abs(h5).max()
+        eh = np.abs(H[0, e] - h5).max() / np.abs(h5).max()
+        eg = np.abs(G[0, e] - g5).max() / np.abs(g5).max()
+        if not near[e]:
+            assert max(eh, eg) < 3e-3, (e, eh, eg)
+        else:
+            assert max(eh, eg) < (5e-3 if dist[e] > 0.8 else 0.15), (e, dist[e], eh, eg)
+            h1, g1 = _subdivided_blocks(x0, g.p[e], g.normal[e], s, mat, 0, Q.rule_4pt)
+            e4 = np.abs(h1 - h5).max() / np.abs(h5).max()
+            assert eh < e4, (e, eh, e4)
