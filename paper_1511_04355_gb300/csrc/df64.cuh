@@ -40,14 +40,17 @@ __device__ __forceinline__ df df_from(double x) {
 }
 __device__ __forceinline__ double df_to(df a) { return (double)a.h + (double)a.l; }
 
+// The error-free sums use the round-to-nearest intrinsics, which the compiler never contracts
+// into an FMA: a product fused into the sum s = a + b would leave s inconsistent with the a that
+// the error term subtracts, and the pair would lose its low part.
 __device__ __forceinline__ df quick2(float a, float b) {  // |a| >= |b|
-  const float s = a + b;
-  return dfm(s, b - (s - a));
+  const float s = __fadd_rn(a, b);
+  return dfm(s, __fsub_rn(b, __fsub_rn(s, a)));
 }
 __device__ __forceinline__ df two_sum2(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return dfm(s, (a - (s - bb)) + (b - bb));
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return dfm(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
 }
 __device__ __forceinline__ df neg(df a) { return dfm(-a.h, -a.l); }
 // Inside expressions the pairs are left unnormalised: the sum of the high parts is split exactly

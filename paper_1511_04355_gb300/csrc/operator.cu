@@ -69,10 +69,12 @@ struct Dist {
   R dx, dy, dz, r, r_lo, rinv;
 };
 
+// Knuth's TwoSum, s + e = a + b exactly; the intrinsics keep the compiler from contracting the
+// products of the squared distance into these sums.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
 __device__ __forceinline__ Dist<float> distance(float px, float py, float pz, float4 pl, float x0,
