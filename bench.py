@@ -52,8 +52,8 @@ FLOPS_PER_UNIT_U = 113   # displacement-kernel (U) columns: the right-hand side 
 FLOPS_PER_UNIT_RES = 221  # fused FP64 residual r = K k - A x: T and U per kernel evaluation
 # The same residual in float-float on the FP32 pipes (resid_df_kernel, lazily renormalised
 # pairs): FP32 flops per kernel evaluation, FADD + FMUL + 2 FFMA thread-instructions of one launch
-# (ncu executed-instruction counters, 16 frequencies on 5120 triangles) divided by its units
-FLOPS_PER_UNIT_RES_DF = 1811
+# (ncu executed-instruction counters, 24 frequencies on 5120 triangles) divided by its units
+FLOPS_PER_UNIT_RES_DF = 1802
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -383,10 +383,10 @@ def run_gpu(args):
 
 
 def kernel_case():
-    """Small case for ncu captures of the operator kernels: the 5120-triangle cavity, 16
-    consecutive benchmark frequencies (s_56 .. s_71, equally spaced: the FP32 operator runs them
-    through its recurrence kernel), one FP32 operator application and one float-float refinement
-    residual, each after a warm-up call."""
+    """Small case for ncu captures of the operator kernels: the 5120-triangle cavity, 24
+    consecutive benchmark frequencies (s_52 .. s_75, equally spaced: the FP32 operator runs them
+    through its recurrence kernel as two CTA groups of 12), one FP32 operator application and
+    one float-float refinement residual, each after a warm-up call."""
     import torch
 
     import paper_1511_04355_gb300 as P
@@ -398,7 +398,7 @@ def kernel_case():
     c.set_material(m.mu, m.nu, m.rho)
     c.set_bc(prob.bc_type, prob.bc_value)
     ne = len(prob.tris)
-    s = prob.s[56:72]
+    s = prob.s[52:76]
     x = torch.from_numpy(W.random_complex_vectors(len(s), 3 * ne) * 1e-6).cuda()
     y = torch.zeros_like(x)
     for _ in range(2):
