@@ -2,7 +2,7 @@
 preconditioner) against the FP64 CPU oracle, through the C ABI.
 
 Sizes: 80 and 320 triangles (ragged against the 128-target and 64/32-source tiles), 5
-frequencies (ragged against the 8- and 4-frequency tiles) including s = sigma (|z| small, the
+frequencies (ragged against the 12- and 4-frequency tiles) including s = sigma (|z| small, the
 series branch) and the top of the benchmark band; traction-given and mixed boundary conditions.
 Tolerances: FP64 path 1e-10 relative (the two sides differ only in rounding order and in the
 |z| threshold of the Taylor branch); FP32 operator 2e-5 relative in the 2-norm (single-precision
@@ -133,6 +133,13 @@ def test_invalid_arguments_are_errors():
         c.element_blocks(250.0, [0], [80])
     with pytest.raises(P.BemError):
         c.set_mesh(np.zeros((3, 3)), np.array([[0, 1, 2]]))       # zero-area triangle
+    c3 = _ctx(1, False)   # the rejected mesh above leaves c without one
+    for call in (lambda: c3.solve(np.zeros(0, complex)),            # empty frequency lists
+                 lambda: c3.apply(np.zeros(0, complex), np.zeros((0, 240), complex)),
+                 lambda: c3.residual(np.zeros(0, complex), np.zeros((0, 240), complex))):
+        with pytest.raises(P.BemError) as e:
+            call()
+        assert e.value.code == P.BEM_ERR_INVALID_ARG
     c2 = P.Context(0)
     with pytest.raises(P.BemError) as e:
         c2.rhs(np.array([250.0]))
