@@ -335,7 +335,7 @@ def run_gpu(args):
     n64, ms64, fl64 = per_step["res64"]
     flops64 = fl64 * (ne * ne - ne) * 4 * FLOPS_PER_UNIT_RES_DF
     ach64 = flops64 / (ms64 / 1e3) / 1e12 if ms64 > 0 else 0.0
-    roof32 = {"kernel": "far_kernel<float> (FP32 far-field operator)", "bound": "alu",
+    roof32 = {"kernel": "far32_kernel (FP32 far-field operator)", "bound": "alu",
               "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
               "traffic": None, "launches_per_step": n32, "ms_per_step": ms32,
               "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (recipe unit counts, max clock)"}
