@@ -55,6 +55,11 @@ FLOPS_PER_UNIT_RES = 221  # fused FP64 residual r = K k - A x: T and U per kerne
 # (ncu executed-instruction counters, 24 frequencies on 5120 triangles) divided by its units
 FLOPS_PER_UNIT_RES_DF = 1802
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# DRAM bytes (read + write) of one FP32 far-kernel launch from an ncu capture of the 24-frequency
+# kernel case (5120 triangles, 24 x 5120 x 5119 x 4 units): the source vectors, the geometry and
+# the FP64 accumulator lines the atomic adds pull in, all proportional to the frequencies (units)
+# of a launch, so the roofline scales it to the benchmark's average launch
+FAR32_CAPTURE_BYTES, FAR32_CAPTURE_UNITS = 9.80864e6, 24 * 5120 * 5119 * 4
 
 
 def workload_config(n_gpus):
@@ -337,7 +342,10 @@ def run_gpu(args):
     ach64 = flops64 / (ms64 / 1e3) / 1e12 if ms64 > 0 else 0.0
     roof32 = {"kernel": "far32_kernel (FP32 far-field operator)", "bound": "alu",
               "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
-              "traffic": None, "launches_per_step": n32, "ms_per_step": ms32,
+              "traffic": (FAR32_CAPTURE_BYTES * (units32 / n32) / FAR32_CAPTURE_UNITS
+                          if n32 and ne == 5120 else None),
+              "traffic_unit": "bytes per launch (ncu 24-frequency capture scaled by units)",
+              "launches_per_step": n32, "ms_per_step": ms32,
               "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (recipe unit counts, max clock)"}
     roof64 = {"kernel": "resid_df_kernel (FP64-class refinement residual r = K k - A x, float-float)",
               "bound": "alu", "achieved": ach64, "peak": peak32, "unit": "TFLOP/s",
