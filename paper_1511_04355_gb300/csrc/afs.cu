@@ -24,6 +24,7 @@
 // e^{a t}.
 #include <chrono>
 #include <cstring>
+#include <future>
 #include <limits>
 
 #include "kernel_math.cuh"
@@ -62,8 +63,11 @@ StepOut afs_step(const std::vector<cd>& s, const std::vector<cd>& F, int nobs, i
   }
   std::vector<int> cols(K);
   for (int k = 0; k < K; ++k) cols[k] = k;
+  // the two fits are independent: f_L on a second host thread (its exceptions rethrown here)
+  auto fut_L = std::async(std::launch::async,
+                          [&] { return vfit::fit_poles(s, Fo, K, cols, ML, p.omega_max, p.vf_iters, 1e-10); });
   const vfit::Poles PH = vfit::fit_poles(s, Fo, K, cols, MH, p.omega_max, p.vf_iters, 1e-10);
-  const vfit::Poles PL = vfit::fit_poles(s, Fo, K, cols, ML, p.omega_max, p.vf_iters, 1e-10);
+  const vfit::Poles PL = fut_L.get();
   StepOut o;
   o.H = vfit::residues(s, F, nobs, PH);
   const vfit::Model L = vfit::residues(s, F, nobs, PL);

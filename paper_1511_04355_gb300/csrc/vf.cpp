@@ -14,10 +14,13 @@
 // [[Re a, Im a], [-Im a, Re a]] with b = (2, 0)), computed by Hessenberg reduction and
 // Francis double-shift QR.  Unstable poles are kept.
 // Residue identification: one QR of Phi, all responses as right-hand sides.
+// The per-response eliminations are independent and run on host threads (each response's
+// arithmetic is unchanged, so the result does not depend on the thread count).
 #include <algorithm>
 #include <cmath>
 #include <complex>
 #include <stdexcept>
+#include <thread>
 #include <vector>
 
 #include "vf_host.h"
@@ -26,6 +29,13 @@ namespace bem {
 namespace vfit {
 
 namespace {
+
+// Worker threads for the per-response eliminations: half the host's hardware threads (the two
+// fits of an AFS step run side by side), at least one.
+int host_threads() {
+  const unsigned h = std::thread::hardware_concurrency();
+  return std::max(1, (int)(h / 2));
+}
 
 // Column-major dense helpers ------------------------------------------------------------------
 struct Mat {
@@ -265,7 +275,7 @@ Poles relocate(const std::vector<cd>& s, const std::vector<cd>& F, int K, const 
     for (int m = 0; m < M; ++m) sc[m] += std::norm(Phi[j][m]);
   for (int m = 0; m < M; ++m) sc[m] = sc[m] > 0 ? std::sqrt(2.0 * sc[m]) : 1.0;
   Mat Rs(Kc * M, M), Ys(Kc * M, 1);
-  for (int kk = 0; kk < Kc; ++kk) {
+  auto eliminate = [&](int kk) {
     const int k = cols[kk];
     Mat A(2 * J, 2 * M), B(2 * J, 1);
     for (int j = 0; j < J; ++j) {
@@ -286,6 +296,18 @@ Poles relocate(const std::vector<cd>& s, const std::vector<cd>& F, int K, const 
       for (int c = 0; c < M; ++c) Rs(kk * M + r, c) = (M + r <= M + c) ? A(M + r, M + c) : 0.0;
       Ys(kk * M + r, 0) = B(M + r, 0);
     }
+  };
+  // responses on host threads once the eliminations are large enough to pay for a thread
+  const int nt = ((double)J * M * M < 2e5) ? 1 : std::min(Kc, host_threads());
+  if (nt <= 1) {
+    for (int kk = 0; kk < Kc; ++kk) eliminate(kk);
+  } else {
+    std::vector<std::thread> pool;
+    for (int w = 0; w < nt; ++w)
+      pool.emplace_back([&, w] {
+        for (int kk = w; kk < Kc; kk += nt) eliminate(kk);
+      });
+    for (auto& th : pool) th.join();
   }
   Mat ct = lstsq(Rs, Ys);
   Mat H(M, M);
