@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <exception>
 #include <stdexcept>
 #include <thread>
 #include <vector>
@@ -302,12 +303,20 @@ Poles relocate(const std::vector<cd>& s, const std::vector<cd>& F, int K, const 
   if (nt <= 1) {
     for (int kk = 0; kk < Kc; ++kk) eliminate(kk);
   } else {
+    // a worker's exception (e.g. an allocation failure) is carried back and rethrown here
+    std::vector<std::exception_ptr> err(nt);
     std::vector<std::thread> pool;
     for (int w = 0; w < nt; ++w)
       pool.emplace_back([&, w] {
-        for (int kk = w; kk < Kc; kk += nt) eliminate(kk);
+        try {
+          for (int kk = w; kk < Kc; kk += nt) eliminate(kk);
+        } catch (...) {
+          err[w] = std::current_exception();
+        }
       });
     for (auto& th : pool) th.join();
+    for (auto& e : err)
+      if (e) std::rethrow_exception(e);
   }
   Mat ct = lstsq(Rs, Ys);
   Mat H(M, M);
