@@ -65,3 +65,24 @@ def test_host_vf_errors():
     P = _P()
     with pytest.raises(P.BemError):
         P.bem_vf_fit(np.array([250 + 0j, 250 + 1j]), np.ones((2, 1)), 5, 10.0)   # M > J
+
+
+def test_host_vf_threaded_size_recovers_poles_and_is_deterministic():
+    """A fit large enough for the per-response eliminations to run on host threads
+    (160 samples, 6 responses, 49 poles): exact pole recovery on rational data, the oracle's
+    poles, and bit-identical results on a repeat."""
+    P = _P()
+    rng = np.random.default_rng(5)
+    modes = -(30 + 120 * rng.random(24)) + 1j * np.sort(rng.uniform(200, 7800, 24))
+    poles = np.concatenate([modes, np.conj(modes), [-400.0 + 0j]])
+    R = rng.standard_normal((6, 24)) + 1j * rng.standard_normal((6, 24))
+    R = np.hstack([R, np.conj(R), rng.standard_normal((6, 1)) + 0j])
+    s = 250 + 1j * np.linspace(0, 8000, 160)
+    F = vf.evaluate(s, poles, R)
+    p1, R1 = P.bem_vf_fit(s, F, 49, 8000.0)
+    p2, R2 = P.bem_vf_fit(s, F, 49, 8000.0)
+    assert np.array_equal(p1, p2) and np.array_equal(R1, R2)
+    assert np.abs(_sorted(p1) - _sorted(poles)).max() < 1e-6 * np.abs(poles).max()
+    assert np.abs(P.bem_vf_eval(p1, R1, s) - F).max() < 1e-9 * np.abs(F).max()
+    po, _ = vf.fit(s, F, 49, 8000.0)
+    assert np.abs(_sorted(p1) - _sorted(po)).max() < 1e-6 * np.abs(poles).max()
