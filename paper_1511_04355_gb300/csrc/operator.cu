@@ -662,7 +662,8 @@ struct Cfg;
 template <>
 struct Cfg<float> {  // FP32: 128 targets x 12 frequencies per CTA, 32-element source tiles
   // (12 rather than 8 amortises each element's geometry over more frequencies while 4 CTAs of
-  // 54 KB shared memory still fit an SM: 5 % faster on the 5120-triangle cavity; 16 left 3)
+  // 54 KB shared memory still fit an SM: 5 % faster on the 5120-triangle cavity; with 16 only
+  // 3 CTAs fit, and it was slower than 12)
   static constexpr int TB = 128, S = 32, FT = 12, kPerSM = 4;
 };
 template <>
