@@ -213,7 +213,8 @@ int bem_fsm(bem_ctx* ctx, double period, double eta, int64_t nc, const double* t
  * BEM_NOALLOC_FSM_TABLE (INVALID_ARG with a message otherwise).  The first call on a device
  * looks up that array's device address, so make it before any stream capture.  All calls share
  * the array: calls that overlap on the GPU race.  Errors: INVALID_ARG (sizes, host pointers,
- * pointers of another device), CUDA; the message is returned by bem_noalloc_last_error(). */
+ * pointers of another device), CUDA; the message is returned by bem_noalloc_last_error(), which
+ * keeps one message per calling thread (valid until that thread's next failing call). */
 #define BEM_NOALLOC_FSM_TABLE 262144
 int bem_fsm_eval_noalloc(const double* h, int64_t nc, int64_t m, double eta, double period,
                          const double* t, int64_t nt, int window, double* out, void* cuda_stream);

@@ -383,11 +383,41 @@ def bem_fsm_eval(ctx, h, eta, period, t, window=1, out=None):
     return out
 
 
+def _require_tensors(specs):
+    """ValueError unless every (name, x, dtype, shape) in specs is a contiguous CUDA tensor of
+    the current device with that dtype and shape (dtypes and shapes are checked for all of them
+    before devices): the C side can only check that it was given device pointers, not how many
+    bytes lie behind them."""
+    import torch
+
+    for name, x, dtype, shape in specs:
+        if not isinstance(x, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if x.dtype != dtype:
+            raise ValueError(f"{name} must have dtype {dtype}, got {x.dtype}")
+        if tuple(x.shape) != tuple(shape):
+            raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(x.shape)}")
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    for name, x, _, _ in specs:
+        if x.device.type != "cuda" or x.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} must be on the current CUDA device, got {x.device}")
+
+
 def bem_fsm_eval_noalloc(h, eta, period, t, out, window=1, stream=None):
-    """Allocation-free FSM inversion: h (nc, m) complex128, t (nt,), out (nt, m) float64 must be
-    CUDA tensors of the current device; stream: a cudaStream_t handle or None."""
+    """Allocation-free FSM inversion: h (nc, m) complex128, t (nt,) float64 and out (nt, m)
+    float64 must be contiguous CUDA tensors of the current device; stream: a cudaStream_t handle
+    or None.  Dtypes and shapes are checked here (ValueError) before the library is called."""
+    import torch
+
+    if not isinstance(h, torch.Tensor) or h.dim() != 2:
+        raise ValueError("h must be a 2-D torch tensor (nc, m)")
+    if not isinstance(t, torch.Tensor) or t.dim() != 1:
+        raise ValueError("t must be a 1-D torch tensor (nt,)")
     nc, m = h.shape
     nt = t.shape[0]
+    _require_tensors([("h", h, torch.complex128, (nc, m)), ("t", t, torch.float64, (nt,)),
+                      ("out", out, torch.float64, (nt, m))])
     rc = load_library().bem_fsm_eval_noalloc(_ptr(h), nc, m, eta, period, _ptr(t), nt, window,
                                              _ptr(out), stream)
     if rc != BEM_OK:

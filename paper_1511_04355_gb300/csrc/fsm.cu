@@ -31,21 +31,26 @@ __global__ void fsm_table_kernel(const double* t, int64_t nt, int64_t nc, double
   E[q] = mk(amp * cs, amp * sn);
 }
 
-// out[j][d] = Re sum_k E[j][k] h[k][d]; grid (ceil(m / 128), nt), E row in shared memory.
+// out[j][d] = Re sum_k E[j][k] h[k][d]; grid (ceil(m / 128), min(nt, 65535)), each block
+// row strides over the times j by gridDim.y (grid y is capped at 65535), the table row of the
+// current time in shared memory.
 __global__ void fsm_apply_kernel(const cx<double>* E, const cx<double>* h, int64_t nt, int64_t nc,
                                  int64_t m, double* out) {
   extern __shared__ cx<double> row[];
-  const int64_t j = blockIdx.y;
-  for (int64_t k = threadIdx.x; k < nc; k += blockDim.x) row[k] = E[j * nc + k];
-  __syncthreads();
   const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (d >= m) return;
-  double acc = 0.0;
-  for (int64_t k = 0; k < nc; ++k) {
-    const cx<double> hv = h[k * m + d];
-    acc = fma(row[k].r, hv.r, fma(-row[k].i, hv.i, acc));
+  for (int64_t j = blockIdx.y; j < nt; j += gridDim.y) {
+    __syncthreads();  // the previous time's row is no longer read
+    for (int64_t k = threadIdx.x; k < nc; k += blockDim.x) row[k] = E[j * nc + k];
+    __syncthreads();
+    if (d < m) {
+      double acc = 0.0;
+      for (int64_t k = 0; k < nc; ++k) {
+        const cx<double> hv = h[k * m + d];
+        acc = fma(row[k].r, hv.r, fma(-row[k].i, hv.i, acc));
+      }
+      out[j * m + d] = acc;
+    }
   }
-  out[j * m + d] = acc;
 }
 
 // Launch both kernels with a caller-provided table (nt x nc complex).
@@ -57,7 +62,8 @@ void fsm_launch(const cx<double>* h, int64_t nc, int64_t m, double eta, double p
   const size_t smem = sizeof(cx<double>) * nc;
   if (smem > 48 * 1024)
     BEM_CUDA(cudaFuncSetAttribute(fsm_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  fsm_apply_kernel<<<dim3(grid_for(m, 128), (unsigned)nt), 128, smem, st>>>(table, h, nt, nc, m, out);
+  const unsigned gy = (unsigned)std::min<int64_t>(nt, 65535);
+  fsm_apply_kernel<<<dim3(grid_for(m, 128), gy), 128, smem, st>>>(table, h, nt, nc, m, out);
   BEM_LAUNCHED();
 }
 

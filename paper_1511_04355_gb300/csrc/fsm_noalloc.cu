@@ -30,7 +30,7 @@ static __device__ __align__(256) cx<double> g_fsm_scratch[kNoAllocTable];
 namespace {
 std::mutex g_mu;
 cx<double>* g_scratch_addr[kMaxDevices] = {nullptr};
-std::string g_err;
+thread_local std::string g_err;  // per calling thread, so the returned pointer stays valid
 
 cx<double>* scratch_for(int dev) {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -57,10 +57,7 @@ void require_device_ptr(const void* p, int dev, const char* name) {
 
 }  // namespace bem
 
-extern "C" const char* bem_noalloc_last_error(void) {
-  std::lock_guard<std::mutex> lk(bem::g_mu);
-  return bem::g_err.c_str();
-}
+extern "C" const char* bem_noalloc_last_error(void) { return bem::g_err.c_str(); }
 
 extern "C" int bem_fsm_eval_noalloc(const double* h, int64_t nc, int64_t m, double eta,
                                     double period, const double* t, int64_t nt, int window,
@@ -86,7 +83,6 @@ extern "C" int bem_fsm_eval_noalloc(const double* h, int64_t nc, int64_t m, doub
     BEM_CUDA(cudaStreamSynchronize(st));
     return BEM_OK;
   } catch (const Error& e) {
-    std::lock_guard<std::mutex> lk(g_mu);
     g_err = e.what();
     return e.code;
   }

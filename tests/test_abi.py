@@ -82,3 +82,28 @@ def test_afs_defaults_are_the_papers_printed_values():
     d = {n: v.default for n, v in inspect.signature(OA.run).parameters.items()}
     for k in ("J0", "alpha_H", "alpha_L", "E1bar", "E2bar", "Jc"):
         assert d[k] == vals[k], k
+
+
+def test_noalloc_binding_refuses_bad_tensors_before_calling_the_library():
+    """The allocation-free FSM wrapper checks dtypes, shapes and devices itself: the library can
+    only see that it was handed device pointers, not how large the buffers behind them are."""
+    torch = pytest.importorskip("torch")
+    import paper_1511_04355_gb300 as P
+
+    nc, m, nt = 8, 5, 7
+    h = torch.zeros((nc, m), dtype=torch.complex128)
+    t = torch.zeros((nt,), dtype=torch.float64)
+    out = torch.zeros((nt, m), dtype=torch.float64)
+    bad = [
+        (h.real.contiguous(), t, out, "dtype"),                            # real h: half the bytes
+        (h, t.float(), out, "dtype"),
+        (h, t, torch.zeros((nt, m + 1), dtype=torch.float64), "shape"),    # out too wide
+        (h, t, torch.zeros((nt - 1, m), dtype=torch.float64), "shape"),    # out too short
+        (h, t, out, "device"),                                             # host tensors
+        (h[None], t, out, "2-D"),
+        (h, t[None], out, "1-D"),
+    ]
+    for hh, tt, oo, word in bad:
+        with pytest.raises(ValueError) as e:
+            P.bem_fsm_eval_noalloc(hh, 250.0, 0.04, tt, oo)
+        assert word in str(e.value), (word, str(e.value))

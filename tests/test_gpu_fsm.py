@@ -39,6 +39,18 @@ def test_fsm_eval_matches_oracle(window, nc, m, nt):
     assert np.abs(out - ref).max() <= 1e-12 * max(np.abs(ref).max(), 1e-300)
 
 
+def test_fsm_eval_more_times_than_one_grid_dimension():
+    """nt = 70000 > 65535 output times (the grid's y limit): every time row is written."""
+    rng = np.random.default_rng(70000)
+    nc, m, nt = 3, 2, 70000
+    h = rng.standard_normal((nc, m)) + 1j * rng.standard_normal((nc, m))
+    t = np.linspace(0.0, 0.04, nt)
+    c = _ctx()
+    out = c.fsm_eval(h, 250.0, 0.04, t, 1)
+    ref = OF.invert(h, 250.0, 0.04, t)
+    assert np.abs(out - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
 def test_fsm_eval_device_pointers():
     import torch
     P = _P()

@@ -39,6 +39,24 @@ def test_noalloc_matches_allocating_entry_point_twice():
         ctx.close()
 
 
+def test_noalloc_more_times_than_one_grid_dimension():
+    """nt = 70000 > 65535 (the grid's y limit) with nc = 2 fits the fixed scratch and every time
+    row is written, matching the allocating entry point."""
+    import torch
+    import paper_1511_04355_gb300 as P
+
+    nc, m, nt = 2, 3, 70000
+    h, t = _case(nc, m, nt, 3)
+    ctx = P.Context(0)
+    try:
+        ref = ctx.fsm_eval(h, 250.0, 0.04, t, 1)
+    finally:
+        ctx.close()
+    od = torch.full((nt, m), float("nan"), dtype=torch.float64, device="cuda")
+    P.bem_fsm_eval_noalloc(torch.from_numpy(h).cuda(), 250.0, 0.04, torch.from_numpy(t).cuda(), od, 1)
+    assert np.abs(od.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
 def test_noalloc_rejects_oversized_table():
     import torch
     import paper_1511_04355_gb300 as P
