@@ -6,13 +6,22 @@ the launch configuration the benchmark uses, on outputs the oracle can compute o
 * Solve: the benchmark's batched mixed-precision solve of all 128 frequencies; every frequency
   reports a certified FP64 residual <= 1e-6, and the oracle's sampled residual rows
   r_i = b_i - (A x)_i, formed from the GPU solution, stay below 1e-6 ||b||.
+* Solution: the same batched solve against the oracle's dense-LU solutions at k = 0, 64, 127
+  (tests/golden/cavity5120_lu.npz, written by make_cavity5120_lu.py from the oracle alone),
+  elementwise: every entry against the largest LU entry.  A residual of tol ||b|| bounds the
+  error by ||A^-1|| ||A|| tol, and the measured amplification reaches ~5 at the top of the band,
+  so the bounds are 1e-5 at the benchmark tolerance 1e-6, 1e-6 at tol 2e-7 (the tolerance at
+  which the mixed path's solutions meet 1e-6) and 1e-8 at tol 1e-9.
 """
+import os
+
 import functools
 
 import numpy as np
 import pytest
 
 import workloads as W
+from _parity import max_rel_err
 from oracle import bem as OB
 
 pytestmark = pytest.mark.gpu
@@ -85,3 +94,27 @@ def test_benchmark_solve_residuals():
         assert np.abs(b[j, rr] - b_rows).max() <= 1e-10 * np.abs(b_rows).max()
         r_rows = b_rows - A @ x[k]
         assert np.abs(r_rows).max() <= 1e-6 * np.linalg.norm(b[j]), k
+
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "cavity5120_lu.npz")
+
+
+@pytest.mark.parametrize("tol,bound", [(1e-6, 1e-5), (2e-7, 1e-6), (1e-9, 1e-8)])
+def test_benchmark_solve_matches_dense_lu_elementwise(tol, bound):
+    import torch
+    import paper_1511_04355_gb300 as P
+    gold = np.load(GOLDEN)
+    prob, _ = _problem()
+    assert np.allclose(gold["s"], prob.s[gold["k"]], rtol=0, atol=1e-9)
+    assert (gold["lu_residual"] < 1e-13).all()
+    c = _ctx()
+    c.set_options(precision=P.BEM_PREC_MIXED, tol=tol)
+    ne = len(prob.tris)
+    sd = torch.from_numpy(prob.s).cuda()
+    xd = torch.zeros((128, 3 * ne), dtype=torch.complex128, device="cuda")
+    _, info = P.bem_solve_frequencies(c.h, sd, xd)
+    assert (info["status"] == 0).all() and (info["residual"] <= tol).all()
+    x = xd.cpu().numpy()
+    errs = [max_rel_err(x[k], xl, prob.bc_type) for k, xl in zip(gold["k"], gold["x"])]
+    print(f"tol {tol}: elementwise error against dense LU at k = {gold['k'].tolist()}: {errs}")
+    assert max(errs) <= bound, errs
