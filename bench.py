@@ -43,7 +43,12 @@ N_FREQ = 128
 T_WIN = 0.02
 SIGMA = 250.0
 TOL = 1e-6
-FP64_SAMPLE = 16     # frequencies of the plain-FP64 comparison (every 8th)
+# Residual tolerance at which the mixed path's solutions meet 1e-6 relative error elementwise
+# (against a tol-1e-9 solve of the same discretisation and the oracle's dense LU): a residual of
+# 1e-6 ||b|| leaves solution errors up to ~5e-6 max|x| at the top of the band
+TOL_ACCURATE = 2e-7
+TOL_REFERENCE = 1e-9
+ACC_ELEMENTS = (0, 700, 1500, 2560, 3333, 4000, 4600, 5119)  # radial displacement responses
 METRIC = "BEM frequency solves/s at 1e-6 rel. residual vs plain FP64 GPU; % FP32 peak"
 # FP32 far-field kernel, traction columns: FP32 flops per kernel evaluation counted from the
 # kernel source (FMA = 2; exp/sin/cos on the special-function unit not counted)
@@ -54,7 +59,13 @@ FLOPS_PER_UNIT_RES = 221  # fused FP64 residual r = K k - A x: T and U per kerne
 # pairs): FP32 flops per kernel evaluation, FADD + FMUL + 2 FFMA thread-instructions of one launch
 # (ncu executed-instruction counters, 24 frequencies on 5120 triangles) divided by its units
 FLOPS_PER_UNIT_RES_DF = 1802
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0  # nominal, for the derived-peak note only
+# Executed flops per kernel evaluation of the far-field kernels (FADD + FMUL + 2 FFMA, resp.
+# DADD + DMUL + 2 DFMA thread instructions from ncu executed-instruction counters divided by the
+# launches' units): the FP32 kernel over every far32 launch of one benchmark solve (the mix of
+# its recurrence and direct instantiations), the FP64 kernel on the 24-frequency kernel case
+FLOPS_EXEC_PER_UNIT_FAR32 = 149.4   # 4.449e13 flop over the 2.978e11 units of one solve's 80 launches
+FLOPS_EXEC_PER_UNIT_FAR64 = 287.4   # 7.231e11 flop over the 2.516e9 units of one launch
 # DRAM bytes (read + write) of one FP32 far-kernel launch from an ncu capture of the 24-frequency
 # kernel case (5120 triangles, 24 x 5120 x 5119 x 4 units): the source vectors, the geometry and
 # the FP64 accumulator lines the atomic adds pull in, all proportional to the frequencies (units)
@@ -292,33 +303,66 @@ def run_gpu(args):
     t_e2e = SH.max_over_ranks(float(np.mean(et)), dev)
     e2e_value = SH.aggregate_rate(N_FREQ, ws, t_e2e)
 
-    # accuracy and the plain-FP64 GPU path on a sample of the band
-    sel = np.arange(0, N_FREQ, N_FREQ // FP64_SAMPLE)
-    x_mixed = x_dev[sel].cpu().numpy()
+    def timed_solve(s_d, x_d):
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, inf = P.bem_solve_frequencies(ctx.h, s_d, x_d)
+        b.record(stream)
+        barrier()
+        return a.elapsed_time(b) / 1e3, inf
+
+    # accuracy: the timed solutions, and the mixed path at the tolerance whose solutions meet
+    # 1e-6 relative error, against a tol-1e-9 solve of the same discretisation (frequency
+    # responses elementwise, radial-displacement time responses by the FSM)
+    x_mixed = x_dev.cpu().numpy()
+    ctx.set_options(precision=P.BEM_PREC_MIXED, tol=TOL_REFERENCE)
+    x_ref_d = torch.zeros_like(x_dev)
+    _, info_ref = P.bem_solve_frequencies(ctx.h, s_dev, x_ref_d)
+    x_ref = x_ref_d.cpu().numpy()
+    ctx.set_options(precision=P.BEM_PREC_MIXED, tol=TOL_ACCURATE)
+    x_acc_d = torch.zeros_like(x_dev)
+    timed_solve(s_dev, x_acc_d)                     # warm-up at this tolerance
+    t_acc, info_acc = timed_solve(s_dev, x_acc_d)
+    x_acc = x_acc_d.cpu().numpy()
+    nrm = W.unit_normals(prob.verts, prob.tris)
+    els = np.array(ACC_ELEMENTS)
+    t_out = np.linspace(0.0, 0.01, 200)
+
+    def radial_time(x):
+        # outward radial displacement of the cavity wall (normals point into the cavity)
+        u = x.reshape(len(x), ne, 3)[:, els, :]
+        ur = -np.einsum("fed,ed->fe", u, nrm[els])
+        return ctx.fsm_eval(np.ascontiguousarray(ur), SIGMA, 2 * T_WIN, t_out, 1)
+
+    h_ref = radial_time(x_ref)
+
+    def errors(x):
+        ew = np.abs(x - x_ref).max(axis=1) / np.abs(x_ref).max(axis=1)
+        ht = radial_time(x)
+        et = np.abs(ht - h_ref).max(axis=0) / np.abs(h_ref).max(axis=0)
+        return float(ew.max()), int(ew.argmax()), float(et.max())
+
+    e_f, k_f, e_t = errors(x_mixed)
+    e_fa, k_fa, e_ta = errors(x_acc)
+
+    # the plain-FP64 GPU path (FP64 operator and GMRES) over all frequencies of the step
     ctx.set_options(precision=P.BEM_PREC_FP64, tol=TOL)
-    s64 = torch.from_numpy(np.ascontiguousarray(s_all[sel])).to(dev)
-    x64 = torch.zeros((len(sel), n_unk), dtype=torch.complex128, device=dev)
-    P.bem_solve_frequencies(ctx.h, s64, x64)        # warm-up of the FP64 path
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    _, info64 = P.bem_solve_frequencies(ctx.h, s64, x64)
-    e1.record(stream)
-    barrier()
-    t64 = e0.elapsed_time(e1) / 1e3
-    fp64_value = len(sel) / t64
-    # the same sample through the mixed path, for a like-for-like ratio
+    x64 = torch.zeros_like(x_dev)
+    P.bem_solve_frequencies(ctx.h, s_dev[:2].contiguous(), x64[:2])   # warm-up of the FP64 path
+    ctx.profile(True)
+    t64, info64 = timed_solve(s_dev, x64)
+    kt64 = ctx.kernel_times()
+    ctx.profile(False)
+    fp64_value = N_FREQ / t64
+    e_f64, _, e_t64 = errors(x64.cpu().numpy())
     ctx.set_options(precision=P.BEM_PREC_MIXED, tol=TOL)
-    xm = torch.zeros_like(x64)
-    barrier()
-    e0.record(stream)
-    P.bem_solve_frequencies(ctx.h, s64, xm)
-    e1.record(stream)
-    barrier()
-    tm = e0.elapsed_time(e1) / 1e3
-    x64h = x64.cpu().numpy()
-    err = np.linalg.norm(x_mixed - x64h, axis=1) / np.linalg.norm(x64h, axis=1)
+
+    # measured FP32 and FP64 peaks (FMA-chain kernels, CUDA events), clocks sampled meanwhile
+    with ClockSampler(local) as clk_peak:
+        peak32, _, n_sm = P.bem_measure_peak(ctx.h, P.BEM_PEAK_FP32, 2048, 5)
+        peak64, _, _ = P.bem_measure_peak(ctx.h, P.BEM_PEAK_FP64, 512, 5)
 
     if rank != 0:
         if ws > 1:
@@ -336,8 +380,12 @@ def run_gpu(args):
     # (active) frequencies; the library counts the frequency-launches
     n32, ms32, fl32 = per_step["far32"]
     units32 = fl32 * (ne * ne - ne) * 4
-    peak32 = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    ach32 = units32 * FLOPS_PER_UNIT_T / (ms32 / 1e3) / 1e12 if ms32 > 0 else 0.0
+    peak_note = (f"measured: FFMA-chain kernel on {n_sm} SMs, best of 5 launches (CUDA events), "
+                 f"SM clock median {clk_peak.summary().get('sm_mhz')} MHz; nominal "
+                 f"{n_sm} SMs x {FP32_LANES} lanes x 2 x {SM_MAX_MHZ:.0f} MHz = "
+                 f"{n_sm * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12:.1f} TFLOP/s")
+    ach32_direct = units32 * FLOPS_PER_UNIT_T / (ms32 / 1e3) / 1e12 if ms32 > 0 else 0.0
+    ach32 = units32 * FLOPS_EXEC_PER_UNIT_FAR32 / (ms32 / 1e3) / 1e12 if ms32 > 0 else 0.0
     # FP64-class refinement residual (fused U + T far-field sweep in float-float on the FP32
     # pipes), one launch per full residual
     n64, ms64, fl64 = per_step["res64"]
@@ -345,16 +393,35 @@ def run_gpu(args):
     ach64 = flops64 / (ms64 / 1e3) / 1e12 if ms64 > 0 else 0.0
     roof32 = {"kernel": "far32_kernel (FP32 far-field operator)", "bound": "alu",
               "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
+              "flop_per_unit": FLOPS_EXEC_PER_UNIT_FAR32,
+              "flop_count": "executed FP32 flops (ncu FADD + FMUL + 2 FFMA thread instructions per "
+                            "kernel evaluation)",
+              "achieved_direct_equivalent": ach32_direct,
+              "frac_direct_equivalent": ach32_direct / peak32,
+              "direct_equivalent_note": f"{FLOPS_PER_UNIT_T} flop per evaluation counted on the direct "
+                                        "formulation (what the frequency recurrence and the per-element "
+                                        "application avoid computing)",
               "traffic": (FAR32_CAPTURE_BYTES * (units32 / n32) / FAR32_CAPTURE_UNITS
                           if n32 and ne == 5120 else None),
               "traffic_unit": "bytes per launch (ncu 24-frequency capture scaled by units)",
-              "launches_per_step": n32, "ms_per_step": ms32,
-              "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (recipe unit counts, max clock)"}
+              "launches_per_step": n32, "ms_per_step": ms32, "peak_note": peak_note}
     roof64 = {"kernel": "resid_df_kernel (FP64-class refinement residual r = K k - A x, float-float)",
               "bound": "alu", "achieved": ach64, "peak": peak32, "unit": "TFLOP/s",
               "frac": ach64 / peak32, "traffic": None, "launches_per_step": n64,
               "ms_per_step": ms64, "flop_per_unit": FLOPS_PER_UNIT_RES_DF,
-              "peak_note": "FP32 pipes: 152 SMs x 128 lanes x 2 x 2070 MHz (recipe unit counts, max clock)"}
+              "flop_count": "executed FP32 flops (ncu FADD + FMUL + 2 FFMA thread instructions per "
+                            "kernel evaluation)", "peak_note": peak_note}
+    # the plain-FP64 path's far kernel (FP64 operator in its GMRES) against the FP64 peak
+    n_f64, ms_f64, fl_f64 = kt64["far64"]
+    ach_f64 = (fl_f64 * (ne * ne - ne) * 4 * FLOPS_EXEC_PER_UNIT_FAR64 / (ms_f64 / 1e3) / 1e12
+               if ms_f64 > 0 else 0.0)
+    roof_fp64 = {"kernel": "far_kernel<double> (FP64 far-field operator of the plain-FP64 path)",
+                 "bound": "alu", "achieved": ach_f64, "peak": peak64, "unit": "TFLOP/s",
+                 "frac": ach_f64 / peak64, "flop_per_unit": FLOPS_EXEC_PER_UNIT_FAR64,
+                 "flop_count": "executed FP64 flops (ncu DADD + DMUL + 2 DFMA thread instructions per "
+                               "kernel evaluation)",
+                 "launches": n_f64, "ms": ms_f64, "share_of_fp64_path": ms_f64 / 1e3 / t64,
+                 "peak_note": "measured: DFMA-chain kernel, best of 5 launches (CUDA events)"}
     roofline = roof64 if dominant == "res64" else roof32
 
     cpu_v, cpu_sample, _ = (None, None, None)
@@ -373,15 +440,31 @@ def run_gpu(args):
         "roofline_fp32_operator": roof32,
         "roofline_residual": roof64,
         "kernel_ms_per_step": {k: v[1] for k, v in per_step.items()},
-        "fp64_gpu_path": {"value": fp64_value, "unit": "solves/s",
-                          "sample": f"{len(sel)} of the {N_FREQ} frequencies (every {N_FREQ // len(sel)}th)",
-                          "mixed_same_sample": len(sel) / tm,
-                          "speedup_mixed_vs_fp64": (len(sel) / tm) / fp64_value,
-                          "iterations": info64["iterations"].tolist()},
-        "accuracy": {"max_fp64_residual": float(np.max(info["residual"])),
-                     "max_rel_err_vs_fp64_gpu_path": float(err.max()),
+        "fp64_gpu_path": {"value": fp64_value, "unit": "solves/s", "seconds": t64,
+                          "sample": f"all {N_FREQ} frequencies of the step, tol {TOL}",
+                          "speedup_mixed_vs_fp64": value / fp64_value,
+                          "iterations": info64["iterations"].tolist(),
+                          "max_rel_err_elementwise": e_f64, "max_rel_err_time": e_t64,
+                          "roofline": roof_fp64},
+        "accuracy": {"reference": f"mixed path at tol {TOL_REFERENCE} (max FP64-class residual "
+                                  f"{float(np.max(info_ref['residual'])):.2e})",
+                     "metric_elementwise": "max_k max_n |x_kn - xref_kn| / max_n |xref_kn|",
+                     "metric_time": f"max over t in [0, 10 ms] of |u_r(t) - u_r,ref(t)| / max |u_r,ref| "
+                                    f"(FSM of the radial displacement at elements {list(ACC_ELEMENTS)})",
+                     "at_tol": {"tol": TOL, "max_fp64_residual": float(np.max(info["residual"])),
+                                "max_rel_err_elementwise": e_f, "worst_frequency": k_f,
+                                "max_rel_err_time": e_t, "solves_per_s": value,
+                                "gmres_iterations": int(np.sum(info["iterations"]))},
+                     "at_accurate_tol": {"tol": TOL_ACCURATE,
+                                         "max_fp64_residual": float(np.max(info_acc["residual"])),
+                                         "max_rel_err_elementwise": e_fa, "worst_frequency": k_fa,
+                                         "max_rel_err_time": e_ta,
+                                         "solves_per_s": SH.aggregate_rate(N_FREQ, ws, t_acc),
+                                         "gmres_iterations": int(np.sum(info_acc["iterations"]))},
                      "iterations": info["iterations"].tolist(),
                      "refinements": info["refinements"].tolist()},
+        "peaks_measured": {"fp32_tflops": peak32, "fp64_tflops": peak64, "sm_count": n_sm,
+                           "clocks": clk_peak.summary()},
     }
     if cpu_v is not None:
         line["cpu_baseline"] = {"value": cpu_v, "unit": "solves/s", "cores": os.cpu_count(),
@@ -415,8 +498,35 @@ def kernel_case():
     for _ in range(2):
         P.bem_apply(c.h, s, x, y, P.BEM_PREC_FP32, P.BEM_APPLY_A)
         P.bem_residual(c.h, s, x, y, P.BEM_RESID_DF64)
+        P.bem_apply(c.h, s, x, y, P.BEM_PREC_FP64, P.BEM_APPLY_A)
     torch.cuda.synchronize()
-    print("kernel case done")
+    print("kernel case done: units per far launch", len(s) * ne * (ne - 1) * 4)
+
+
+def profile_step():
+    """One mixed solve of the benchmark step (128 frequencies, tol 1e-6) with the library's
+    per-class kernel timing on: prints the far32 launches and their frequency-launches, i.e. the
+    units (x ne (ne - 1) 4) an ncu capture of this command's far32 launches divides by."""
+    import torch
+
+    import paper_1511_04355_gb300 as P
+
+    prob = W.spherical_cavity(level=LEVEL, n_freq=N_FREQ, T=T_WIN, sigma=SIGMA)
+    c = P.Context(0)
+    c.set_mesh(prob.verts, prob.tris)
+    m = prob.material
+    c.set_material(m.mu, m.nu, m.rho)
+    c.set_bc(prob.bc_type, prob.bc_value, P.BEM_PROFILE_STEP)
+    c.set_options(precision=P.BEM_PREC_MIXED, tol=TOL)
+    ne = len(prob.tris)
+    c.profile(True)
+    x, info = c.solve(prob.s)
+    kt = c.kernel_times()
+    torch.cuda.synchronize()
+    n32, ms32, fl32 = kt["far32"]
+    print(json.dumps({"far32_launches": n32, "far32_freq_launches": fl32,
+                      "far32_units": fl32 * ne * (ne - 1) * 4, "far32_ms": ms32,
+                      "gmres_iterations": int(info["iterations"].sum())}))
 
 
 def workload_uneven():
@@ -466,29 +576,80 @@ def workload_uneven():
     print(json.dumps(line), flush=True)
 
 
-def workload_porous_afs(full=False):
-    """The porous-block workload: a 1 m block with 27 seeded spherical voids (radii 0.08-0.15 m),
-    traction on z = 0, z = 1 fixed; the step response of six unknowns by a 256-frequency FSM and
-    by AFS over the same band, both through the library.  full: the ~30000-triangle recipe
-    (42 x 42 grid per face, level-2 voids) over the configured band (T = 20 ms); else a reduced
-    mesh (20 x 20 per face, level-1 voids, 6960 triangles) over the band it resolves (T = 50 ms:
-    Omega = 255 pi / T ~ 16000 rad/s, ~5.5 elements per shear wavelength).  GMRES(200): box
-    problems with a fixed face need hundreds of iterations at the upper frequencies, where
-    GMRES(50) restarts stall."""
+def afs_vs_fsm(label, pb, dofs, n_orf, period, nc, J0, warm, restart=200, extra=None):
+    """AFS (Sec. 3) against the FSM (Sec. 2.2) on one problem through the library: the FSM solves
+    the nc frequencies eta + i k 2 pi / period at once; AFS samples the same band [0, Omega],
+    Omega = (nc - 1) 2 pi / period, adaptively, with its first n_orf unknowns as observation
+    responses and the rest as test unknowns.  eta = 3 ln(10) / period (Sec. 2.2 with the kappa =
+    3 of Sec. 4).  The transients are compared over the first half of the period, against the
+    FSM with the Hanning window (the paper's) and without it (the same band-limited information
+    as the fit: the window smooths what the truncated band leaves).  Prints one JSON line."""
     import paper_1511_04355_gb300 as P
 
-    if full:
-        pb = W.porous_block(n=(42, 42, 42), n_voids=27, void_level=2)
-    else:
-        pb = W.porous_block(n=(20, 20, 20), n_voids=27, void_level=1)
     v, f, m = pb["verts"], pb["tris"], pb["material"]
     c = P.Context(0)
     c.set_mesh(v, f)
     c.set_material(m.mu, m.nu, m.rho)
     c.set_bc(pb["bc_type"], pb["bc_value"], P.BEM_PROFILE_STEP)
-    c.set_options(precision=P.BEM_PREC_MIXED, tol=TOL, restart=200, max_iters=4000, max_refine=20)
+    c.set_options(precision=P.BEM_PREC_MIXED, tol=TOL, restart=restart, max_iters=6000, max_refine=20,
+                  warm_start=P.BEM_WARM_ZERO)
+    eta = 3.0 * math.log(10.0) / period
+    omega = (nc - 1) * 2.0 * math.pi / period
+    t = np.linspace(0.0, 0.5 * period, 201)
+    # the FSM: one batched solve of the nc frequencies, inverted with and without the window
+    t0 = time.perf_counter()
+    x, finfo = c.solve(eta + 1j * np.arange(nc) * 2.0 * math.pi / period)
+    h = np.ascontiguousarray(x[:, dofs])
+    fsm_w = c.fsm_eval(h, eta, period, t, 1)
+    t_fsm = time.perf_counter() - t0
+    fsm_n = c.fsm_eval(h, eta, period, t, 0)
+    del x
+    print(json.dumps({"label": label, "fsm_seconds": t_fsm, "triangles": len(f),
+                      "fsm_iterations": int(finfo["iterations"].sum())}), file=sys.stderr, flush=True)
+    c.set_options(precision=P.BEM_PREC_MIXED, tol=TOL, restart=restart, max_iters=6000, max_refine=20,
+                  warm_start=warm)
+    prm = P.bem_default_afs_params(eta=eta, omega_max=omega, T=period, J0=J0, max_samples=nc)
+    t0 = time.perf_counter()
+    afs_out, info = c.afs(prm, dofs[:n_orf], dofs[n_orf:], t)
+    t_afs = time.perf_counter() - t0
+
+    def rel(a, b):
+        return (np.sqrt(np.sum((a - b) ** 2, axis=0) / np.sum(b ** 2, axis=0))).tolist()
+
+    line = {"workload": label, "triangles": len(f), "unknowns": 3 * len(f),
+            "eta": eta, "period": period, "omega_max": omega,
+            "fsm": {"n_c": nc, "seconds": t_fsm, "gmres_iterations": int(finfo["iterations"].sum())},
+            "afs": {"n_c": int(info["n_samples"]), "seconds": t_afs, "poles": len(info["poles"]),
+                    "E1": float(info["E1"][-1]), "E2": float(info["E2"][-1]),
+                    "seconds_solve": info["seconds_solve"], "seconds_fit": info["seconds_fit"],
+                    "seconds_train": info["seconds_train"],
+                    "gmres_iterations": int(np.sum(info["gmres_iters"])),
+                    "warm_start": {0: "zero", 1: "nearest", 2: "mlp"}[warm]},
+            "afs_vs_fsm_rel_l2": {"hanning": rel(afs_out, fsm_w), "no_window": rel(afs_out, fsm_n)},
+            "fsm_hanning_vs_no_window_rel_l2": rel(fsm_w, fsm_n),
+            "nc_ratio_fsm_over_afs": nc / max(int(info["n_samples"]), 1)}
+    if extra:
+        line.update(extra)
+    print(json.dumps(line), flush=True)
+    c.close()
+
+
+def workload_porous_afs(full=False):
+    """The porous-block workload: a 1 m block with 27 seeded spherical voids (radii 0.08-0.15 m),
+    traction on z = 0, z = 1 fixed; the step response of six unknowns by a 256-frequency FSM and
+    by AFS over the same band.  full: the ~30000-triangle recipe (42 x 42 grid per face, level-2
+    voids) over a 40 ms period; else a reduced mesh (20 x 20 per face, level-1 voids, 6960
+    triangles) over a 100 ms period (Omega = 255 pi / 0.05 ~ 16000 rad/s, ~5.5 elements per shear
+    wavelength).  GMRES(200): box problems with a fixed face need hundreds of iterations at the
+    upper frequencies, where GMRES(50) restarts stall."""
+    if full:
+        pb = W.porous_block(n=(42, 42, 42), n_voids=27, void_level=2)
+    else:
+        pb = W.porous_block(n=(20, 20, 20), n_voids=27, void_level=1)
+    v, f = pb["verts"], pb["tris"]
     face = pb["face"]
     cent = v[f].mean(axis=1)
+
     def nearest(mask, target):
         idx = np.flatnonzero(mask)
         return int(idx[np.argmin(np.linalg.norm(cent[idx] - target, axis=1))])
@@ -498,28 +659,39 @@ def workload_porous_afs(full=False):
                      3 * int(voids[0]) + 2, 3 * int(voids[len(voids) // 2]) + 2,
                      3 * nearest(face == 4, [0.25, 0.75, 0.0]) + 2,
                      3 * int(voids[-1]) + 2])
-    t_win = T_WIN if full else 0.05
-    period, nc = 2 * t_win, 256
-    omega = (nc - 1) * math.pi / t_win
-    t = np.linspace(0.0, 0.5 * t_win, 201)
-    t0 = time.perf_counter()
-    fsm_out, _ = c.fsm(period, SIGMA, nc, t, dofs)
-    t_fsm = time.perf_counter() - t0
-    print(json.dumps({"porous_fsm_seconds": t_fsm, "triangles": len(f)}), file=sys.stderr, flush=True)
-    prm = P.bem_default_afs_params(eta=SIGMA, omega_max=omega, T=period, J0=8, max_samples=200)
-    t0 = time.perf_counter()
-    afs_out, info = c.afs(prm, dofs[:4], dofs[4:], t)
-    t_afs = time.perf_counter() - t0
-    late = t > 0.1 * t_win
-    rel = np.sqrt(np.sum((afs_out[late] - fsm_out[late]) ** 2, axis=0) / np.sum(fsm_out[late] ** 2, axis=0))
-    line = {"workload": f"porous block 1x1x1 m, 27 voids, {len(f)} triangles ({3 * len(f)} unknowns), "
-                        f"step traction on z=0, z=1 fixed; band {omega:.0f} rad/s",
-            "fsm": {"n_c": nc, "seconds": t_fsm},
-            "afs": {"n_c": int(info["n_samples"]), "seconds": t_afs, "poles": len(info["poles"]),
-                    "E1": float(info["E1"][-1]), "E2": float(info["E2"][-1]),
-                    "seconds_solve": info["seconds_solve"], "seconds_fit": info["seconds_fit"]},
-            "afs_vs_fsm_rel_l2_late": rel.tolist(), "window_s": t_win}
-    print(json.dumps(line), flush=True)
+    period = 2 * T_WIN if full else 0.1
+    label = (f"porous block 1x1x1 m, 27 voids, {len(f)} triangles ({3 * len(f)} unknowns), step traction "
+             "on z=0, z=1 fixed")
+    afs_vs_fsm(label, pb, dofs, 4, period, 256, 8, 0)
+
+
+def workload_example3(warm=0, n=(12, 12, 18), void_level=1):
+    """The paper's third example (Sec. 4, Example 3): the 1 x 1 x 1.5 m aluminium block with 98
+    cavities of radius 0.072 m, fixed on z = 1.5, step traction on z = 0; period T = 0.035 s, FSM
+    with N_s = 478 (N_c = 240) against AFS with the paper's parameters (J0 = 16, alpha 2.0 / 2.3,
+    E1 < 1e-4, E2 < 2e-3, J_c = 3) and six observation responses (two tractions on the fixed
+    face, four displacements), two test unknowns (u_z on the loaded face, t_z on the fixed face).
+    The paper reports N_c = 240 (FSM) against 61 (AFS) for its 18080 quadratic elements."""
+    pb = W.example3_block(n=n, void_level=void_level)
+    v, f = pb["verts"], pb["tris"]
+    face = pb["face"]
+    cent = v[f].mean(axis=1)
+
+    def nearest(mask, target):
+        idx = np.flatnonzero(mask)
+        return int(idx[np.argmin(np.linalg.norm(cent[idx] - target, axis=1))])
+    cav = np.flatnonzero(face < 0)
+    dofs = np.array([3 * nearest(face == 5, [0.3, 0.4, 1.5]) + 2,        # t_z, fixed face
+                     3 * nearest(face == 5, [0.7, 0.2, 1.5]) + 2,        # t_z, fixed face
+                     3 * nearest(face == 4, [0.5, 0.5, 0.0]) + 2,        # u_z, loaded face
+                     3 * nearest(face == 0, [0.0, 0.5, 0.75]) + 0,       # u_x, side face
+                     3 * int(cav[len(cav) // 3]) + 2,                    # u_z, a cavity wall
+                     3 * nearest(face == 2, [0.5, 0.0, 1.0]) + 1,        # u_y, side face
+                     3 * nearest(face == 4, [0.74, 0.34, 0.0]) + 2,      # test: u_z, loaded face
+                     3 * nearest(face == 5, [0.6, 0.8, 1.5]) + 2])       # test: t_z, fixed face
+    label = (f"block 1x1x1.5 m with 98 cavities r=0.072 m (Example 3), aluminium, {len(f)} triangles "
+             f"({3 * len(f)} unknowns), fixed z=1.5, step traction on z=0")
+    afs_vs_fsm(label, pb, dofs, 6, 0.035, 240, 16, warm, extra={"paper_nc": {"fsm": 240, "afs": 61}})
 
 
 def main():
@@ -531,17 +703,26 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the small operator/residual case used for ncu captures")
-    ap.add_argument("--workload", choices=["uneven", "porous-afs", "porous-afs-full"],
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run one benchmark solve with kernel counts (for ncu instruction counters)")
+    ap.add_argument("--workload", choices=["uneven", "porous-afs", "porous-afs-full", "example3",
+                                           "example3-mlp"],
                     help="run one of the other workloads instead of the benchmark (own JSON line)")
     args = ap.parse_args()
     if args.kernel_case:
         kernel_case()
+        return
+    if args.profile_step:
+        profile_step()
         return
     if args.workload == "uneven":
         workload_uneven()
         return
     if args.workload in ("porous-afs", "porous-afs-full"):
         workload_porous_afs(full=args.workload == "porous-afs-full")
+        return
+    if args.workload in ("example3", "example3-mlp"):
+        workload_example3(warm=2 if args.workload == "example3-mlp" else 0)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -312,7 +312,10 @@ typedef struct bem_afs_params {
                         variant, to keep the GPU batched): the paper's s_new, then further
                         argmaxes of the same discrepancy curve after masking +-Omega/(2J)
                         around each pick, kept while >= 0.1 of the first; solved together    */
-  int32_t reserved[5];
+  int32_t warm_retrain; /* with the context's warm_start = BEM_WARM_MLP: retrain the network
+                        once this many samples have been added since its last training
+                        (0: 4).  Ignored for the other warm-start modes                       */
+  int32_t reserved[4];
 } bem_afs_params;
 
 typedef struct bem_afs_stats {
@@ -326,6 +329,10 @@ typedef struct bem_afs_stats {
   int64_t n_steps;   /* out: AFS steps (entries written to E1 / E2)                       */
   int32_t n_poles;   /* out: order of the final fit                                       */
   double seconds_solve, seconds_fit; /* out: time in BEM solves / in fitting             */
+  double seconds_train;     /* out: time spent training the warm-start network            */
+  int32_t warm_trainings;   /* out: trainings of the warm-start network                   */
+  int32_t warm_nearest_picks; /* out: learned-start solves that fell back to the nearest
+                               stored solution (smaller initial residual)                 */
 } bem_afs_stats;
 
 /* Fill *p with the paper's parameter values (Sec. 3.4) and the defaults above; eta,
@@ -337,6 +344,12 @@ int bem_default_afs_params(bem_afs_params* p);
  * BEM system (one batched GPU solve, the context's options) at the frequency where the fits
  * disagree most, and stops when the time-domain change E1 and the fit discrepancy E2 of the
  * test unknowns test[Kt] stay below their thresholds for Jc + 1 consecutive steps.
+ * Warm start: when the context's warm_start option is BEM_WARM_NEAREST or BEM_WARM_MLP, the call
+ * first clears the warm-start memory, then stores every solution it computes (up to 256) and so
+ * starts each new frequency's GMRES from the solutions already sampled; with BEM_WARM_MLP it
+ * trains the network (default bem_warm_params) after the initial frequencies and again every
+ * params->warm_retrain new samples, and falls back per frequency to the nearest stored solution
+ * when that leaves the smaller initial residual.  The GMRES tolerance is unchanged. 
  * resp_out[nt_out x (K + Kt)] (host or device): time responses of the ORFs then the test
  * unknowns at t_out[nt_out] (Eq. (vf-td), final fit); stats nullable.
  * Errors: INVALID_ARG, NOT_CONVERGED (a frequency solve failed), NO_MESH, CUDA. */
@@ -403,6 +416,56 @@ int bem_profile(bem_ctx* ctx, int enable);
  * number of frequencies the launches covered (each far/near launch computes the listed active
  * frequencies only).  Any output pointer may be NULL.  Errors: INVALID_ARG (bad kind). */
 int bem_kernel_time(bem_ctx* ctx, int kind, int64_t* launches, double* ms, int64_t* freq_launches);
+
+/* ------------------------------------------------------------------ launch tuning
+ * The FP32 far-field launch (the operator's hot loop) has three shape parameters:
+ *   ft    frequencies one CTA evaluates together (4, 8 or 12): each source point's geometry is
+ *         formed once and reused for them;
+ *   tiles 32-element source tiles a CTA sums in FP32 before its FP64 atomic add;
+ *   waves the source range is split until the grid holds waves x SMs x resident CTAs per SM.
+ * The best shape depends on the mesh size and on how many frequencies a launch carries (GMRES
+ * retires converged frequencies, so late launches carry few).  Without a table every launch uses
+ * ft 12, tiles 2, waves 4.  A table is a list of entries; a launch on a mesh of ne elements with
+ * nfl frequencies uses, among the entries with the smallest ne_max >= ne (else the largest
+ * ne_max), the one with the smallest nfl_max >= nfl (else the largest nfl_max).  The paper has
+ * no counterpart (its solver runs on a CPU). */
+typedef struct bem_tune_entry {
+  int64_t ne_max;   /* the entry applies to meshes of at most ne_max elements ...            */
+  int32_t nfl_max;  /* ... and to launches of at most nfl_max frequencies                    */
+  int32_t ft, tiles, waves;
+  double ms;        /* bem_autotune output: one operator application's time with this shape */
+  double ms_fixed;  /* bem_autotune output: the same with the fixed shape (12, 2, 4)        */
+} bem_tune_entry;
+
+/* Autotuner: for the context's mesh (material and boundary conditions set), and for launches of
+ * the first nfl[j] frequencies of s (j < n_nfl, each <= ns), times one FP32 operator application
+ * (far-field launches + near field) for every shape (ft in {4, 8, 12}, tiles in {1, 2, 4}, waves in {2, 4, 8}; CUDA events, best of 2
+ * after a warm-up) and keeps the fastest.  out[n_nfl] (host): the chosen entries (ne_max = the
+ * mesh's ne).  They are also installed in the context (replacing entries with the same ne_max).
+ * Errors: INVALID_ARG (sizes, nfl[j] outside [1, ns]), NO_MESH, OOM, CUDA. */
+int bem_autotune(bem_ctx* ctx, const double* s, int64_t ns, const int32_t* nfl, int32_t n_nfl,
+                 bem_tune_entry* out);
+/* Install a table of n entries (host; copied), replacing the context's table; n = 0 restores
+ * the fixed shape.  Errors: INVALID_ARG (an entry with ft not 4, 8 or 12, tiles or waves < 1). */
+int bem_set_tuning(bem_ctx* ctx, const bem_tune_entry* table, int32_t n);
+/* Read a table from a text file (one entry per line: ne_max nfl_max ft tiles waves [ms ms_fixed]; '#'
+ * starts a comment; ms and ms_fixed are optional) and install it.  Errors: INVALID_ARG (unreadable file or bad line). */
+int bem_load_tuning(bem_ctx* ctx, const char* path);
+/* The shape a far-field launch of nfl frequencies on the context's mesh would use. */
+int bem_launch_shape(bem_ctx* ctx, int64_t nfl, int32_t* ft, int32_t* tiles, int32_t* waves);
+
+/* Measured arithmetic peak of the context's device, the denominator of the ALU-bound kernels'
+ * rooflines (the paper has no counterpart: the operator and the refinement residual are bound by
+ * the FP32 pipes, the plain-FP64 path by the FP64 pipes).  A kernel fills every SM with
+ * independent fused multiply-add chains (FFMA for BEM_PEAK_FP32, DFMA for BEM_PEAK_FP64; 2 flops
+ * each), iters x 128 steps per chain, launched reps times on the context's stream after one
+ * warm-up launch and timed with CUDA events.  Out (host, each nullable): *tflops = the best
+ * launch's rate, *ms_best = its duration, *sm_count = the device's multiprocessor count.
+ * Errors: INVALID_ARG (kind, iters < 1, reps < 1), OOM, CUDA. */
+#define BEM_PEAK_FP32 0
+#define BEM_PEAK_FP64 1
+int bem_measure_peak(bem_ctx* ctx, int kind, int32_t iters, int32_t reps, double* tflops,
+                     double* ms_best, int32_t* sm_count);
 
 #ifdef __cplusplus
 }

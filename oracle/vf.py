@@ -122,11 +122,32 @@ def residues(s, F, pairs, reals):
     return np.array(poles), np.array(R).T
 
 
+SAMPLE_GAP = 1e-6   # relocated poles keep at least this fraction of Omega from every sample
+
+
+def keep_off_samples(s, pairs, reals, omega_max):
+    """A relocated pole closer than SAMPLE_GAP * Omega to a sample s_j is moved to s_j - SAMPLE_GAP
+    * Omega (the same imaginary part, left of the sampling line): the samples lie to the right of
+    the physical poles (Re s = eta > 0) and unstable poles are kept, so with noisy data an extra
+    pole can settle on a sample, where the basis 1/(s - a) of the next step is infinite.  The paper
+    is silent on this case."""
+    s = np.asarray(s)
+    gap = SAMPLE_GAP * omega_max
+
+    def fix(a):
+        sj = s[np.argmin(np.abs(s - a))]
+        return sj - gap if abs(sj - a) < gap else a
+
+    return (np.array([fix(a) for a in pairs], dtype=complex),
+            np.array([np.real(fix(a)) for a in reals], dtype=float))
+
+
 def fit(s, F, M, omega_max, n_iter=20, tol=1e-10, init=None):
     """Vector fit of order M: (poles (M,), residues (K, M)) with pairs expanded."""
     pairs, reals = init if init is not None else initial_poles(M, omega_max)
     for _ in range(n_iter):
         p2, r2 = pole_identification(s, F, pairs, reals)
+        p2, r2 = keep_off_samples(s, p2, r2, omega_max)
         if len(p2) == len(pairs) and len(r2) == len(reals):
             change = max(np.abs(p2 - pairs).max(initial=0.0), np.abs(r2 - reals).max(initial=0.0))
             pairs, reals = p2, r2

@@ -45,6 +45,8 @@ BEM_KERNEL_NEAR64 = 3
 BEM_KERNEL_SELF = 4
 BEM_KERNEL_VEC = 5
 BEM_KERNEL_RES64 = 6
+BEM_PEAK_FP32 = 0
+BEM_PEAK_FP64 = 1
 KERNEL_NAMES = {0: "far32", 1: "far64", 2: "near32", 3: "near64", 4: "self", 5: "gmres_vec",
                 6: "res64"}
 
@@ -74,7 +76,7 @@ class bem_afs_params(C.Structure):
                 ("alpha_H", C.c_double), ("alpha_L", C.c_double), ("E1bar", C.c_double),
                 ("E2bar", C.c_double), ("J0", C.c_int32), ("Jc", C.c_int32), ("n_grid", C.c_int32),
                 ("nt", C.c_int32), ("max_samples", C.c_int32), ("vf_iters", C.c_int32),
-                ("batch", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("batch", C.c_int32), ("warm_retrain", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class bem_afs_stats(C.Structure):
@@ -82,7 +84,9 @@ class bem_afs_stats(C.Structure):
                 ("gmres_iters", C.POINTER(C.c_int32)), ("E1", C.POINTER(C.c_double)),
                 ("E2", C.POINTER(C.c_double)), ("poles", C.POINTER(C.c_double)),
                 ("n_samples", C.c_int64), ("n_steps", C.c_int64), ("n_poles", C.c_int32),
-                ("seconds_solve", C.c_double), ("seconds_fit", C.c_double)]
+                ("seconds_solve", C.c_double), ("seconds_fit", C.c_double),
+                ("seconds_train", C.c_double), ("warm_trainings", C.c_int32),
+                ("warm_nearest_picks", C.c_int32)]
 
 
 class bem_warm_params(C.Structure):
@@ -93,6 +97,12 @@ class bem_warm_params(C.Structure):
 class bem_warm_stats(C.Structure):
     _fields_ = [("r", C.c_int32), ("n_snapshots", C.c_int32), ("loss_first", C.c_double),
                 ("loss_last", C.c_double), ("seconds", C.c_double)]
+
+
+class bem_tune_entry(C.Structure):
+    _fields_ = [("ne_max", C.c_int64), ("nfl_max", C.c_int32), ("ft", C.c_int32),
+                ("tiles", C.c_int32), ("waves", C.c_int32), ("ms", C.c_double),
+                ("ms_fixed", C.c_double)]
 
 
 class bem_batch_item(C.Structure):
@@ -142,6 +152,13 @@ _SIGS = {
                           C.POINTER(bem_solve_stats)]),
     "bem_kernel_time": (C.c_int, [_P, C.c_int, C.POINTER(_I64), C.POINTER(C.c_double),
                                   C.POINTER(_I64)]),
+    "bem_measure_peak": (C.c_int, [_P, C.c_int, C.c_int32, C.c_int32, C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_int32)]),
+    "bem_autotune": (C.c_int, [_P, _P, _I64, _P, C.c_int32, C.POINTER(bem_tune_entry)]),
+    "bem_set_tuning": (C.c_int, [_P, C.POINTER(bem_tune_entry), C.c_int32]),
+    "bem_load_tuning": (C.c_int, [_P, C.c_char_p]),
+    "bem_launch_shape": (C.c_int, [_P, _I64, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int32)]),
 }
 
 _lib = None
@@ -521,7 +538,9 @@ def bem_afs(ctx, params, orf, test, t_out, capacity=1024):
     n, ns, npol = st.n_samples, st.n_steps, st.n_poles
     info = dict(s=arr["s"][:n], gmres_iters=arr["gmres_iters"][:n], E1=arr["E1"][:ns],
                 E2=arr["E2"][:ns], poles=arr["poles"][:npol], n_samples=n,
-                seconds_solve=st.seconds_solve, seconds_fit=st.seconds_fit)
+                seconds_solve=st.seconds_solve, seconds_fit=st.seconds_fit,
+                seconds_train=st.seconds_train, warm_trainings=st.warm_trainings,
+                warm_nearest_picks=st.warm_nearest_picks)
     return out, info
 
 
@@ -596,6 +615,52 @@ def bem_kernel_time(ctx, kind):
     _check(ctx, load_library().bem_kernel_time(ctx, kind, C.byref(n), C.byref(ms), C.byref(fl)),
            "bem_kernel_time")
     return n.value, ms.value, fl.value
+
+
+TUNING_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "far32_tuning.txt")
+
+
+def bem_autotune(ctx, s, nfl):
+    """Time every FP32 far-field launch shape for launches of the first nfl[j] frequencies of s on
+    the context's mesh; returns the chosen entries as dicts (also installed in the context)."""
+    s, ns = _cplx_as_pairs(s)
+    n = np.ascontiguousarray(nfl, dtype=np.int32)
+    out = (bem_tune_entry * len(n))()
+    _check(ctx, load_library().bem_autotune(ctx, _ptr(s), ns, _ptr(n), len(n), out), "bem_autotune")
+    return [dict(ne_max=e.ne_max, nfl_max=e.nfl_max, ft=e.ft, tiles=e.tiles, waves=e.waves, ms=e.ms,
+                 ms_fixed=e.ms_fixed) for e in out]
+
+
+def bem_set_tuning(ctx, entries):
+    """Install a list of entry dicts (ne_max, nfl_max, ft, tiles, waves[, ms]); [] = fixed shape."""
+    arr = (bem_tune_entry * max(len(entries), 1))()
+    for a, e in zip(arr, entries):
+        a.ne_max, a.nfl_max, a.ft, a.tiles, a.waves = (e["ne_max"], e["nfl_max"], e["ft"], e["tiles"],
+                                                        e["waves"])
+        a.ms = e.get("ms", 0.0)
+        a.ms_fixed = e.get("ms_fixed", 0.0)
+    _check(ctx, load_library().bem_set_tuning(ctx, arr, len(entries)), "bem_set_tuning")
+
+
+def bem_load_tuning(ctx, path=TUNING_TABLE):
+    _check(ctx, load_library().bem_load_tuning(ctx, path.encode()), "bem_load_tuning")
+
+
+def bem_launch_shape(ctx, nfl):
+    ft, tiles, waves = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(ctx, load_library().bem_launch_shape(ctx, nfl, C.byref(ft), C.byref(tiles), C.byref(waves)),
+           "bem_launch_shape")
+    return ft.value, tiles.value, waves.value
+
+
+def bem_measure_peak(ctx, kind, iters=2048, reps=5):
+    """(TFLOP/s of the best launch, its milliseconds, SM count) of the FMA-chain peak kernel."""
+    tf = C.c_double()
+    ms = C.c_double()
+    sm = C.c_int32()
+    _check(ctx, load_library().bem_measure_peak(ctx, kind, iters, reps, C.byref(tf), C.byref(ms),
+                                                C.byref(sm)), "bem_measure_peak")
+    return tf.value, ms.value, sm.value
 
 
 class Context:

@@ -215,8 +215,21 @@ int bem_afs(bem_ctx* ctx, const bem_afs_params* prm, const int64_t* orf, int64_t
     DevBuf ddofs, obs;
     ddofs.reserve(sizeof(int64_t) * nobs);
     copy_in(ctx, ddofs.p, dofs.data(), sizeof(int64_t) * nobs);
-    double t_solve = 0, t_fit = 0;
+    double t_solve = 0, t_fit = 0, t_train = 0;
     std::vector<int32_t> solve_iters;
+    // warm start: the memory holds this run's own samples only
+    const int wmode = ctx->opt.warm_start;
+    const int retrain = p.warm_retrain > 0 ? p.warm_retrain : 4;
+    constexpr int kWarmCap = 256;  // solutions the network can be trained on
+    int warm_trainings = 0, last_train = 0;
+    int64_t nearest_picks = 0;
+    if (wmode != BEM_WARM_ZERO) {
+      ctx->warm.s.clear();
+      ctx->warm.trained = false;
+      ctx->warm.r = 0;
+    }
+    bem_warm_params wprm;
+    bem_default_warm_params(&wprm);
     // one batched solve of the listed frequencies, observed unknowns back to the host
     auto solve = [&](const std::vector<cd>& sl, std::vector<cd>& Fout) {
       const auto t0 = std::chrono::steady_clock::now();
@@ -240,7 +253,21 @@ int bem_afs(bem_ctx* ctx, const bem_afs_params* prm, const int64_t* orf, int64_t
       Fout.resize(F * nobs);
       for (int64_t q = 0; q < F * nobs; ++q) Fout[q] = cd(h[q].r, h[q].i);
       for (int64_t f = 0; f < F; ++f) solve_iters.push_back(it[f]);
+      nearest_picks += ctx->warm_nearest_picks;
+      if (wmode != BEM_WARM_ZERO) {
+        const int64_t room = kWarmCap - (int64_t)ctx->warm.s.size() / 2;
+        if (room > 0) warm_store(ctx, sr.data(), std::min(F, room), ctx->io_a.as<cx<double>>());
+      }
       t_solve += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      // the learned start: train after the initial frequencies, then every `retrain` samples
+      const int J = (int)(ctx->warm.s.size() / 2);
+      if (wmode == BEM_WARM_MLP && J >= 2 && (warm_trainings == 0 || J - last_train >= retrain)) {
+        const auto t1 = std::chrono::steady_clock::now();
+        warm_train(ctx, wprm, nullptr);
+        t_train += std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
+        ++warm_trainings;
+        last_train = J;
+      }
     };
     std::vector<cd> s, F;
     for (int j = 0; j < p.J0; ++j)
@@ -326,6 +353,9 @@ int bem_afs(bem_ctx* ctx, const bem_afs_params* prm, const int64_t* orf, int64_t
       st->n_poles = (int32_t)so.H.poles.size();
       st->seconds_solve = t_solve;
       st->seconds_fit = t_fit;
+      st->seconds_train = t_train;
+      st->warm_trainings = warm_trainings;
+      st->warm_nearest_picks = (int32_t)nearest_picks;
       const int64_t cap = st->capacity;
       for (int64_t j = 0; j < (int64_t)s.size() && j < cap; ++j) {
         if (st->s) {

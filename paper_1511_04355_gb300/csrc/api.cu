@@ -151,6 +151,7 @@ int bem_create(bem_ctx** out, int device, void* stream) {
     BEM_CUDA(cudaSetDevice(device));
     c = new bem_ctx();
     c->device = device;
+    BEM_CUDA(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device));
     bem_default_options(&c->opt);
     if (stream) {
       c->stream = (cudaStream_t)stream;

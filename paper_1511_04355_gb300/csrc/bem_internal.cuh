@@ -120,6 +120,12 @@ struct FarGroup {
   float ws_hi, ws_lo, wp_hi, wp_lo;
 };
 
+// Shape of an FP32 far-field launch (see bem_tune_entry): frequencies per CTA, source tiles a
+// CTA sums before its FP64 atomic add, and the grid's target in waves of resident CTAs.
+struct FarShape {
+  int ft = 12, tiles = 2, waves = 4;
+};
+
 // Four packed doubles (centroid + h, normal + area, quadrature point + weight).
 struct alignas(32) D4 {
   double x, y, z, w;
@@ -267,6 +273,12 @@ struct bem_ctx {
   bem::DevBuf yacc;             // FP64 far-field accumulator [F][ne][3] complex
   int64_t launches = 0;         // kernels launched (accumulated, reset per call)
   int64_t f32_applies = 0, f64_applies = 0;
+  std::vector<bem_tune_entry> tune;  // FP32 far-field launch shapes (empty: FarShape defaults)
+  bool tune_forced = false;          // the autotuner's trial shape overrides the table
+  bem::FarShape tune_force;
+  int n_sm = 0;                      // multiprocessors of the device
+  int64_t warm_nearest_picks = 0; // frequencies of the last solve whose learned start fell back
+                                  // to the nearest stored solution
   // kernel timing
   bool prof = false;
   std::vector<bem::ProfRec> prof_recs;
@@ -331,6 +343,9 @@ struct ProfScope {
   ~ProfScope();
 };
 void prof_collect(bem_ctx* ctx);  // synchronises and folds finished records into totals
+
+// tune.cu: the shape of an FP32 far-field launch of nfl frequencies on the context's mesh
+FarShape far32_shape(bem_ctx* ctx, int64_t nfl);
 
 // fsm.cu
 void fsm_check_args(int64_t nc, int64_t m, double eta, double period, int64_t nt, int window);

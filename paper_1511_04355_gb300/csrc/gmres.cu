@@ -477,28 +477,60 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
     ctx->launches++;
     BEM_CUDA(cudaMemcpyAsync(W.r.p, W.b.p, sizeof(cx<double>) * F * N, cudaMemcpyDeviceToDevice, st));
   }
-  const bool warm = o.warm_start != BEM_WARM_ZERO && ctx->warm.N == N && !ctx->warm.s.empty();
+  const bool warm = o.warm_start != BEM_WARM_ZERO && ctx->warm.N == N && !ctx->warm.s.empty() &&
+                    (o.warm_start == BEM_WARM_NEAREST || ctx->warm.trained);
+  ctx->warm_nearest_picks = 0;
   if (warm) {
     // direction x^ from the warm start, y = A x^ with the operator of the inner solve's
-    // precision, then x0 = alpha x^ and r = b - alpha y with the alpha minimising |r|
-    warm_initial(ctx, o.warm_start, ctx->fs.s.data(), F, x_dev);
-    if (mixed) {
-      DevBuf xf, yf;
-      xf.reserve(sizeof(cx<float>) * F * N);
-      yf.reserve(sizeof(cx<float>) * F * N);
-      narrow_array(ctx, x_dev, xf.as<cx<float>>(), F * N);
-      apply_operator32(ctx, xf.as<cx<float>>(), yf.as<cx<float>>(), BEM_APPLY_A, nullptr);
-      warm_scale_kernel<float><<<(unsigned)F, 256, 0, st>>>(W.r.as<cx<double>>(), yf.as<cx<float>>(), x_dev,
-                                                             W.r.as<cx<double>>(), N);
-    } else {
-      apply_operator64(ctx, x_dev, W.Ax.as<cx<double>>(), BEM_APPLY_A, nullptr);
-      warm_scale_kernel<double><<<(unsigned)F, 256, 0, st>>>(W.b.as<cx<double>>(), W.Ax.as<cx<double>>(), x_dev,
-                                                              W.r.as<cx<double>>(), N);
+    // precision, then x0 = alpha x^ and r = b - alpha y with the alpha minimising |r|.  With the
+    // learned start, the nearest stored solution is the fallback: both candidates are scaled and
+    // each frequency keeps the one with the smaller initial residual.
+    const cx<double>* bsrc = mixed ? W.r.as<cx<double>>() : W.b.as<cx<double>>();
+    auto candidate = [&](int mode, cx<double>* x, cx<double>* r, double* rn2) {
+      warm_initial(ctx, mode, ctx->fs.s.data(), F, x);
+      if (mixed) {
+        DevBuf xf, yf;
+        xf.reserve(sizeof(cx<float>) * F * N);
+        yf.reserve(sizeof(cx<float>) * F * N);
+        narrow_array(ctx, x, xf.as<cx<float>>(), F * N);
+        apply_operator32(ctx, xf.as<cx<float>>(), yf.as<cx<float>>(), BEM_APPLY_A, nullptr);
+        warm_scale_kernel<float><<<(unsigned)F, 256, 0, st>>>(bsrc, yf.as<cx<float>>(), x, r, N);
+      } else {
+        apply_operator64(ctx, x, W.Ax.as<cx<double>>(), BEM_APPLY_A, nullptr);
+        warm_scale_kernel<double><<<(unsigned)F, 256, 0, st>>>(bsrc, W.Ax.as<cx<double>>(), x, r, N);
+      }
+      ctx->launches++;
+      BEM_LAUNCHED();
+      norm2_kernel<double><<<(unsigned)F, 256, 0, st>>>(r, N, nullptr, rn2);
+      ctx->launches++;
+    };
+    DevBuf r1;
+    r1.reserve(sizeof(cx<double>) * F * N);
+    candidate(o.warm_start, x_dev, r1.as<cx<double>>(), W.rn2.as<double>());
+    if (o.warm_start == BEM_WARM_MLP) {
+      DevBuf x2, r2, n2;
+      x2.reserve(sizeof(cx<double>) * F * N);
+      r2.reserve(sizeof(cx<double>) * F * N);
+      n2.reserve(sizeof(double) * F);
+      candidate(BEM_WARM_NEAREST, x2.as<cx<double>>(), r2.as<cx<double>>(), n2.as<double>());
+      std::vector<double> a1(F), a2(F);
+      BEM_CUDA(cudaMemcpyAsync(a1.data(), W.rn2.p, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
+      BEM_CUDA(cudaMemcpyAsync(a2.data(), n2.p, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
+      BEM_CUDA(cudaStreamSynchronize(st));
+      for (int64_t f = 0; f < F; ++f) {
+        if (!(a2[f] < a1[f])) continue;
+        BEM_CUDA(cudaMemcpyAsync(x_dev + f * N, x2.as<cx<double>>() + f * N, sizeof(cx<double>) * N,
+                                 cudaMemcpyDeviceToDevice, st));
+        BEM_CUDA(cudaMemcpyAsync(r1.as<cx<double>>() + f * N, r2.as<cx<double>>() + f * N,
+                                 sizeof(cx<double>) * N, cudaMemcpyDeviceToDevice, st));
+        BEM_CUDA(cudaMemcpyAsync(W.rn2.as<double>() + f, n2.as<double>() + f, sizeof(double),
+                                 cudaMemcpyDeviceToDevice, st));
+        ctx->warm_nearest_picks++;
+      }
+      BEM_CUDA(cudaStreamSynchronize(st));  // x2, r2, n2 are freed on return from this block
     }
-    ctx->launches++;
-    BEM_LAUNCHED();
-    norm2_kernel<double><<<(unsigned)F, 256, 0, st>>>(W.r.as<cx<double>>(), N, nullptr, W.rn2.as<double>());
-    ctx->launches++;
+    BEM_CUDA(cudaMemcpyAsync(W.r.p, r1.p, sizeof(cx<double>) * F * N, cudaMemcpyDeviceToDevice, st));
+    BEM_CUDA(cudaStreamSynchronize(st));
   } else {
     // x = 0, r = b
     BEM_CUDA(cudaMemsetAsync(x_dev, 0, sizeof(cx<double>) * F * N, st));
@@ -590,8 +622,12 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
       // The first inner solve stops at 0.8 tol: below that its own residual drops under the FP32
       // operator's error floor (~1e-6 at the top of the band), so further iterations are lost to
       // the refinement that follows anyway.  Later solves correct a small d, whose FP32 product
-      // is accurate, and stop at 0.5 tol.
-      tgt[f] = std::max(o.inner_tol * rn, (full_done[f] ? 0.5 : 0.8) * o.tol * bnrm);
+      // is accurate, and stop at 0.5 tol.  The relative reduction inner_tol is measured against
+      // |b| in the first solve: its right-hand side and, after a warm start, its initial residual
+      // b - alpha A x^ carry the FP32 operator's error (~1e-7 |b|), so a reduction relative to a
+      // small warm-start residual would chase that error.  Later solves start from an FP64-class
+      // residual and reduce it by inner_tol.
+      tgt[f] = std::max(o.inner_tol * (full_done[f] ? rn : bnrm), (full_done[f] ? 0.5 : 0.8) * o.tol * bnrm);
     }
     if (nwork == 0) break;
     if (total_inner >= o.max_iters) break;

@@ -361,6 +361,7 @@ void warm_store(bem_ctx* ctx, const double* s, int64_t ns, const cx<double>* x_d
   if (ws.N != N) {
     ws.s.clear();
     ws.N = N;
+    ws.trained = false;
   }
   const int64_t old = (int64_t)ws.s.size() / 2;
   const int64_t cap = old + ns;
@@ -373,7 +374,8 @@ void warm_store(bem_ctx* ctx, const double* s, int64_t ns, const cx<double>* x_d
   std::swap(ws.X.p, grown.p);
   std::swap(ws.X.bytes, grown.bytes);
   ws.s.insert(ws.s.end(), s, s + 2 * ns);
-  ws.trained = false;
+  // a trained model stays usable: its basis and network describe the solutions stored when it
+  // was trained; bem_warm_train refits it to the grown memory
 }
 
 void warm_train(bem_ctx* ctx, const bem_warm_params& prm, bem_warm_stats* out) {

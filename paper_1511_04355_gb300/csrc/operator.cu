@@ -752,11 +752,55 @@ int64_t stage_flist(bem_ctx* ctx, const std::vector<int32_t>* flist, int rec_ft)
   return n;
 }
 
+// Resident CTAs per SM of an FP32 far-kernel instantiation (occupancy query, cached).
+template <int FT, bool REC>
+static int far32_per_sm() {
+  static int n = 0;
+  if (!n) {
+    constexpr int TB = Cfg<float>::TB, S = Cfg<float>::S;
+    const size_t smem = far_smem<float, TB, S, FT, false>();
+    BEM_CUDA(cudaFuncSetAttribute(far32_kernel<TB, S, FT, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    int b = 0;
+    BEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, far32_kernel<TB, S, FT, REC>, TB, smem));
+    n = std::max(b, 1);
+  }
+  return n;
+}
+
+// Grid of a far-field launch: targets x CTA frequency groups x source splits, with the split
+// chosen so that the grid covers `waves` waves of resident CTAs and no CTA sums more than
+// `tiles` source tiles before its FP64 atomic add.
+static int64_t far_split(int64_t ne, int64_t tb, int64_t groups, int S, int n_sm, int per_sm, int waves, int tiles,
+                         int64_t* chunk_out) {
+  const int64_t want = (int64_t)waves * n_sm * per_sm;
+  int64_t nsplit = std::max<int64_t>(1, (want + tb * groups - 1) / (tb * groups));
+  nsplit = std::max<int64_t>(nsplit, (ne + (int64_t)tiles * S - 1) / ((int64_t)tiles * S));
+  nsplit = std::min<int64_t>(nsplit, 65535);
+  int64_t chunk = (ne + nsplit - 1) / nsplit;
+  chunk = ((chunk + S - 1) / S) * S;
+  *chunk_out = chunk;
+  return (ne + chunk - 1) / chunk;
+}
+
+template <int FT, bool REC>
+static void launch_far32(bem_ctx* ctx, FarArgs<float>& a, int64_t ng, const FarShape& sh) {
+  constexpr int TB = Cfg<float>::TB, S = Cfg<float>::S;
+  const int64_t tb = grid_for(a.ne, TB), groups = REC ? ng : grid_for(a.nfl, FT);
+  const int64_t nsplit = far_split(a.ne, tb, groups, S, ctx->n_sm > 0 ? ctx->n_sm : 152, far32_per_sm<FT, REC>(),
+                                   sh.waves, sh.tiles, &a.chunk);
+  const size_t smem = far_smem<float, TB, S, FT, false>();
+  const dim3 grid((unsigned)tb, (unsigned)groups, (unsigned)nsplit);
+  BEM_CUDA(cudaFuncSetAttribute(far32_kernel<TB, S, FT, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  far32_kernel<TB, S, FT, REC><<<grid, TB, smem, ctx->stream>>>(a);
+}
+
 // One far-field launch.  REC: over the group descriptors [g0, g0 + ng); else over the list
-// entries [off, off + nfl), FT per CTA.
+// entries [off, off + nfl), FT per CTA (FP32: the launch shape's ft).
 template <class R, bool RESID, bool REC>
 static void launch_far_part(bem_ctx* ctx, const cx<R>* x, int which, int64_t off, int64_t nfl, int64_t g0,
-                            int64_t ng) {
+                            int64_t ng, const FarShape& sh) {
   constexpr int TB = Cfg<R>::TB, S = Cfg<R>::S, FT = Cfg<R>::FT;
   if (nfl <= 0) return;
   FarArgs<R> a;
@@ -778,26 +822,22 @@ static void launch_far_part(bem_ctx* ctx, const cx<R>* x, int which, int64_t off
   a.ne = ctx->mesh.ne;
   a.F = ctx->fs.F;
   a.m = Geo<R>::m(ctx);
-  // split the sources so that the grid covers about four waves of resident CTAs
-  const int64_t tb = grid_for(a.ne, TB), groups = REC ? ng : grid_for(nfl, FT);
-  // and so that a CTA sums at most 2 source tiles in R precision before the FP64 atomic add
-  // (shorter FP32 chains, and more CTAs to balance the tail: 3 % faster solves than 8 tiles)
-  const int64_t want = 4 * 152 * Cfg<R>::kPerSM;
-  int64_t nsplit = std::max<int64_t>(1, (want + tb * groups - 1) / (tb * groups));
-  nsplit = std::max<int64_t>(nsplit, (a.ne + 2 * S - 1) / (2 * S));
-  nsplit = std::min<int64_t>(nsplit, 65535);
-  int64_t chunk = (a.ne + nsplit - 1) / nsplit;
-  chunk = ((chunk + S - 1) / S) * S;
-  nsplit = (a.ne + chunk - 1) / chunk;
-  a.chunk = chunk;
-  const size_t smem = far_smem<R, TB, S, FT, RESID>();
-  const dim3 grid((unsigned)tb, (unsigned)groups, (unsigned)nsplit);
   ProfScope ps(ctx, RESID ? PK_RES64 : (sizeof(R) == 4 ? PK_FAR32 : PK_FAR64), nfl);
   if constexpr (sizeof(R) == 4 && !RESID) {
-    BEM_CUDA(cudaFuncSetAttribute(far32_kernel<TB, S, FT, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
-    far32_kernel<TB, S, FT, REC><<<grid, TB, smem, ctx->stream>>>(a);
+    // the launch shape (frequencies per CTA, tiles per CTA, waves) from the tuning table
+    switch (sh.ft) {
+      case 4: launch_far32<4, REC>(ctx, a, ng, sh); break;
+      case 8: launch_far32<8, REC>(ctx, a, ng, sh); break;
+      default: launch_far32<12, REC>(ctx, a, ng, sh); break;
+    }
   } else {
+    // split the sources so that the grid covers about four waves of resident CTAs and a CTA
+    // sums at most 2 source tiles before the FP64 atomic add
+    const int64_t tb = grid_for(a.ne, TB), groups = REC ? ng : grid_for(nfl, FT);
+    const int64_t nsplit = far_split(a.ne, tb, groups, S, ctx->n_sm > 0 ? ctx->n_sm : 152, Cfg<R>::kPerSM, 4, 2,
+                                     &a.chunk);
+    const size_t smem = far_smem<R, TB, S, FT, RESID>();
+    const dim3 grid((unsigned)tb, (unsigned)groups, (unsigned)nsplit);
     BEM_CUDA(cudaFuncSetAttribute(far_kernel<R, TB, S, FT, RESID>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     far_kernel<R, TB, S, FT, RESID><<<grid, TB, smem, ctx->stream>>>(a);
@@ -809,13 +849,13 @@ static void launch_far_part(bem_ctx* ctx, const cx<R>* x, int which, int64_t off
 // Far field over the staged list: FP32 equally spaced runs (the leading rec_entries) by the
 // recurrence kernel, the rest by the direct one.
 template <class R, bool RESID>
-static void launch_far(bem_ctx* ctx, const cx<R>* x, int which, int64_t nfl) {
+static void launch_far(bem_ctx* ctx, const cx<R>* x, int which, int64_t nfl, const FarShape& sh = FarShape()) {
   const int64_t nrec = ctx->rec_entries;
   if constexpr (sizeof(R) == 4 && !RESID) {
-    launch_far_part<R, RESID, true>(ctx, x, which, 0, nrec, 0, (int64_t)ctx->groups_h.size());
-    launch_far_part<R, RESID, false>(ctx, x, which, nrec, nfl - nrec, 0, 0);
+    launch_far_part<R, RESID, true>(ctx, x, which, 0, nrec, 0, (int64_t)ctx->groups_h.size(), sh);
+    launch_far_part<R, RESID, false>(ctx, x, which, nrec, nfl - nrec, 0, 0, sh);
   } else {
-    launch_far_part<R, RESID, false>(ctx, x, which, 0, nfl, 0, 0);
+    launch_far_part<R, RESID, false>(ctx, x, which, 0, nfl, 0, 0, sh);
   }
 }
 
@@ -874,9 +914,10 @@ void residual64(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::vec
 
 void apply_operator32(bem_ctx* ctx, const cx<float>* x, cx<float>* y, int which,
                       const std::vector<int32_t>* flist) {
-  const int64_t n = stage_flist(ctx, flist, Cfg<float>::FT);
+  const FarShape sh = far32_shape(ctx, flist ? (int64_t)flist->size() : ctx->fs.F);
+  const int64_t n = stage_flist(ctx, flist, sh.ft);
   if (!n) return;
-  launch_far<float, false>(ctx, x, which, n);
+  launch_far<float, false>(ctx, x, which, n, sh);
   launch_near<float>(ctx, x, y, which, n, false);
   ctx->f32_applies++;
 }

@@ -378,11 +378,34 @@ Model residues(const std::vector<cd>& s, const std::vector<cd>& F, int K, const 
   return out;
 }
 
+// A relocated pole closer than 1e-6 Omega to a sample s_j moves to s_j - 1e-6 Omega (same
+// imaginary part, left of the sampling line).  The samples lie right of the physical poles
+// (Re s = eta > 0) and unstable poles are kept, so with noisy data a surplus pole can settle on
+// a sample, where the next step's basis 1/(s - a) is infinite; the paper is silent on this case.
+static void keep_off_samples(const std::vector<cd>& s, Poles& P, double omega_max) {
+  const double gap = 1e-6 * omega_max;
+  auto nearest = [&](cd a) {
+    size_t jb = 0;
+    for (size_t j = 1; j < s.size(); ++j)
+      if (std::abs(s[j] - a) < std::abs(s[jb] - a)) jb = j;
+    return s[jb];
+  };
+  for (cd& a : P.pairs) {
+    const cd sj = nearest(a);
+    if (std::abs(sj - a) < gap) a = sj - gap;
+  }
+  for (double& a : P.reals) {
+    const cd sj = nearest(cd(a, 0.0));
+    if (std::abs(sj - cd(a, 0.0)) < gap) a = sj.real() - gap;
+  }
+}
+
 Poles fit_poles(const std::vector<cd>& s, const std::vector<cd>& F, int K, const std::vector<int>& cols,
                 int M, double omega_max, int n_iter, double tol) {
   Poles P = initial_poles(M, omega_max);
   for (int it = 0; it < n_iter; ++it) {
     Poles Q = relocate(s, F, K, cols, P);
+    keep_off_samples(s, Q, omega_max);
     double change = 0.0;
     const bool same = Q.pairs.size() == P.pairs.size() && Q.reals.size() == P.reals.size();
     if (same) {

@@ -141,3 +141,70 @@ def test_afs_several_new_frequencies_per_step(batch):
     ex = CF.cavity_ur_time(res.t, 1.0, m.mu, m.nu, m.rho, W.CAVITY_P0)
     assert np.abs(res.h[:, 1] - ex).max() < 1e-8 * np.abs(ex).max()
     assert len(res.s) < 64
+
+
+# ---------------------------------------------------------------------------------------------
+# A finite elastic body: undamped modes (poles on the imaginary axis) and the step pole at 0.
+# Sec. 2.2 sets the sampling abscissa eta = kappa ln(10) / T with kappa in [2, 3] (kappa = 3 in
+# Sec. 4); the fitted time response of Eq. (vf-td) carries e^{a t} for every pole left of the
+# line, so a pole misplaced by the data's noise at 0 < Re a < eta grows by up to e^{eta T} over
+# the window.  With kappa = 3 (e^{eta T} = 1e3) AFS converges on data with 1e-7 relative noise;
+# with eta T = 25 (e^{eta T} ~ 7e10) the same data keep E1 large and AFS reaches its cap.
+UNDAMPED = np.array([1760.0, 2090.0, 3390.0, 3850.0, 5200.0, 6100.0])
+
+
+def _undamped_body(seed=3):
+    rng = np.random.default_rng(seed)
+    rm = (rng.standard_normal((len(UNDAMPED), 3)) + 1j * rng.standard_normal((len(UNDAMPED), 3))) * 0.1
+    r0 = rng.standard_normal(3)
+
+    def f_s(s):
+        s = np.asarray(s)[:, None]
+        out = r0[None, :] / s + 0j
+        for w, r in zip(UNDAMPED, rm):
+            out = out + r[None, :] / (s - 1j * w) + np.conj(r)[None, :] / (s + 1j * w)
+        return out
+
+    def f_t(t):
+        t = np.asarray(t)[:, None]
+        out = np.repeat(r0[None, :], len(t), 0)
+        for w, r in zip(UNDAMPED, rm):
+            out = out + 2.0 * np.real(r[None, :] * np.exp(1j * w * t))
+        return out
+
+    return f_s, f_t
+
+
+def _noisy(f_s, level, seed=5):
+    rng = np.random.default_rng(seed)
+
+    def solve(sl):
+        f = f_s(sl)
+        return f * (1.0 + level * (rng.standard_normal(f.shape) + 1j * rng.standard_normal(f.shape)))
+
+    return solve
+
+
+def test_afs_on_undamped_body_needs_the_papers_damping():
+    f_s, f_t = _undamped_body()
+    P, omega = 0.1, 63 * math.pi / 0.05
+    t = np.linspace(0.0, P, 400)
+    eta = fsm.eta_from_kappa(3.0, P)
+    res = afs.run(_noisy(f_s, 1e-7), eta, omega, P, orf=[0, 1, 2], test=[0, 1, 2], J0=8, max_samples=60)
+    assert len(res.s) < 60 and res.E1[-1] < 1e-4 and res.E2[-1] < 2e-3
+    h = vf.time_response(t, res.poles, res.R, eta)
+    assert np.abs(h - f_t(t)).max() < 5e-3 * np.abs(f_t(t)).max()
+    # eta T = 25: same data model, no convergence within the cap, a transient off by far more
+    res2 = afs.run(_noisy(f_s, 1e-7), 250.0, omega, P, orf=[0, 1, 2], test=[0, 1, 2], J0=8, max_samples=60)
+    assert len(res2.s) == 60 and res2.E1[-1] > 1e-4
+    h2 = vf.time_response(t, res2.poles, res2.R, 250.0)
+    assert np.abs(h2 - f_t(t)).max() > 10 * np.abs(h - f_t(t)).max()
+
+
+def test_relocated_pole_is_kept_off_the_samples():
+    s = 69.0 + 1j * np.linspace(0.0, 4000.0, 9)
+    gap = vf.SAMPLE_GAP * 4000.0
+    pairs, reals = vf.keep_off_samples(s, np.array([s[3] + 0.1 * gap, 10.0 + 700j]),
+                                       np.array([69.0 - 0.3 * gap, -5.0]), 4000.0)
+    assert pairs[0] == s[3] - gap and pairs[1] == 10.0 + 700j
+    assert reals[0] == 69.0 - gap and reals[1] == -5.0

@@ -267,6 +267,57 @@ def porous_block(L=(1.0, 1.0, 1.0), n=(8, 8, 8), n_voids=27, radii=(0.08, 0.15),
 
 
 # ----------------------------------------------------------------------------------------------
+# block with 98 spherical cavities (the paper's third example)
+# ----------------------------------------------------------------------------------------------
+ALUMINIUM = Material(mu=69e9 / (2.0 * 1.3), nu=0.3, rho=2.7e3)   # E = 69 GPa, nu = 0.3
+
+
+def example3_cavity_centres(L=(1.0, 1.0, 1.5), layers=7):
+    """Centres of the 98 identical cavities: `layers` equally spaced layers along z, each with
+    14 cavities in four staggered rows of 4, 3, 4 and 3 (rows at y = 1/8, 3/8, 5/8, 7/8 of Ly;
+    rows of 4 at x = 1/8 .. 7/8 of Lx, rows of 3 at x = 1/4, 1/2, 3/4).  The paper states 98
+    identical cavities equally distributed in the block; its figure is not available, so this
+    arrangement is a reading of that sentence."""
+    L = np.asarray(L, dtype=np.float64)
+    cs = []
+    for k in range(layers):
+        z = (k + 0.5) * L[2] / layers
+        for row, y in enumerate((0.125, 0.375, 0.625, 0.875)):
+            xs = (0.125, 0.375, 0.625, 0.875) if row % 2 == 0 else (0.25, 0.5, 0.75)
+            for x in xs:
+                cs.append((x * L[0], y * L[1], z))
+    return np.array(cs)
+
+
+def example3_block(n=(12, 12, 18), void_level=1, radius=0.072, p0=CAVITY_P0, material=ALUMINIUM):
+    """The elastic block of the paper's third example: 1 x 1 x 1.5 m with 98 identical spherical
+    cavities of radius 0.072 m (example3_cavity_centres), fixed on z = 1.5, uniform step traction
+    p0 along +z (into the block) on z = 0, every other surface and every cavity traction-free;
+    aluminium.  The box faces are split into the squares of the grid n, two triangles each; each
+    cavity is an icosphere of 20 * 4**void_level triangles.  Returns a porous_block-like record."""
+    L = np.array([1.0, 1.0, 1.5])
+    bv, bt, fid = box_surface(L, n)
+    centres = example3_cavity_centres(L)
+    verts, tris, off = [bv], [bt], len(bv)
+    for c in centres:
+        v, f = icosphere(void_level, radius, c, inward=True)
+        verts.append(v)
+        tris.append(f + off)
+        off += len(v)
+    verts = np.vstack(verts)
+    tris = np.vstack(tris).astype(np.int32)
+    ne = len(tris)
+    face = np.full(ne, -1, dtype=np.int32)
+    face[:len(bt)] = fid
+    bc_type = np.zeros(ne, dtype=np.int8)
+    bc_value = np.zeros((ne, 3))
+    bc_value[face == 4, 2] = p0
+    bc_type[face == 5] = 1
+    return dict(verts=verts, tris=tris, face=face, material=material, bc_type=bc_type,
+                bc_value=bc_value, centres=centres, radii=np.full(len(centres), radius))
+
+
+# ----------------------------------------------------------------------------------------------
 # prismatic rod
 # ----------------------------------------------------------------------------------------------
 ROD_MATERIAL = Material(mu=2.11e11 / 2.0, nu=0.0, rho=7.85e3)   # E = 2.11e11 Pa, nu = 0
