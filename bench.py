@@ -531,8 +531,9 @@ def profile_step():
 
 def workload_uneven():
     """The uneven-instance workload: 16 ellipsoidal cavities (icosphere levels 2-5, 320-20480
-    triangles, their own materials), 64 frequencies each, solved one context after another and
-    then all together through bem_solve_batch (one host worker and one stream per context)."""
+    triangles, their own materials), 64 frequencies each, all solved together through
+    bem_solve_batch (one host worker and one stream per context), once with the fixed FP32
+    launch shape and once with the shapes of the committed tuning table (far32_tuning.txt)."""
     import torch
 
     import paper_1511_04355_gb300 as P
@@ -541,7 +542,7 @@ def workload_uneven():
     s = W.fsm_frequencies(T_WIN, SIGMA, 64)
     ctxs = []
     for v, f, mat in insts:
-        c = P.Context(0)
+        c = P.Context(0, tuning=False)
         c.set_mesh(v, f)
         c.set_material(mat.mu, mat.nu, mat.rho)
         c.set_bc(np.zeros(len(f), np.int8), W.pressure_pattern(v, f), P.BEM_PROFILE_STEP)
@@ -551,28 +552,26 @@ def workload_uneven():
     # warm-up (allocations, module load)
     P.bem_solve_batch([(c.h, s[:2], o[:2]) for c, o in zip(ctxs, outs)])
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    seq_info = []
-    for k, (c, o) in enumerate(zip(ctxs, outs)):
-        t1 = time.perf_counter()
-        seq_info.append(c.solve(s, o)[1])
-        info = seq_info[-1]
-        print(json.dumps({"instance": k, "triangles": c.ne, "seconds": time.perf_counter() - t1,
-                          "iterations": int(info["iterations"].sum()),
-                          "max_refinements": int(info["refinements"].max())}), file=sys.stderr, flush=True)
-    t_seq = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    res = P.bem_solve_batch([(c.h, s, o) for c, o in zip(ctxs, outs)])
-    t_bat = time.perf_counter() - t0
     n = len(s) * len(ctxs)
-    ok = all((info["status"] == 0).all() and (info["residual"] <= TOL).all() for _, info in res)
+    runs = {}
+    for mode in ("fixed", "tuned"):
+        for c in ctxs:
+            if mode == "fixed":
+                P.bem_set_tuning(c.h, [])
+            else:
+                P.bem_load_tuning(c.h, P.TUNING_TABLE)
+        t0 = time.perf_counter()
+        res = P.bem_solve_batch([(c.h, s, o) for c, o in zip(ctxs, outs)])
+        t_bat = time.perf_counter() - t0
+        ok = all((info["status"] == 0).all() and (info["residual"] <= TOL).all() for _, info in res)
+        runs[mode] = {"seconds": t_bat, "solves_per_s": n / t_bat, "all_certified": bool(ok),
+                      "iterations_total": int(sum(int(i["iterations"].sum()) for _, i in res))}
+        print(json.dumps({"mode": mode, **runs[mode]}), file=sys.stderr, flush=True)
     line = {"workload": "16 uneven ellipsoidal cavities (icosphere levels 2-5, 320-20480 triangles), "
-                        "64 frequencies each, mixed path to 1e-6",
+                        "64 frequencies each, mixed path to 1e-6, solved together by bem_solve_batch",
             "triangles": [len(f) for _, f, _ in insts], "solves": n,
-            "sequential": {"seconds": t_seq, "solves_per_s": n / t_seq},
-            "batched": {"seconds": t_bat, "solves_per_s": n / t_bat},
-            "speedup_batched_vs_sequential": t_seq / t_bat, "all_certified": bool(ok),
-            "iterations_total": int(sum(int(i["iterations"].sum()) for i in seq_info))}
+            "fixed_launch_shape": runs["fixed"], "autotuned_launch_shapes": runs["tuned"],
+            "speedup_tuned_vs_fixed": runs["fixed"]["seconds"] / runs["tuned"]["seconds"]}
     print(json.dumps(line), flush=True)
 
 
@@ -694,6 +693,56 @@ def workload_example3(warm=0, n=(12, 12, 18), void_level=1):
     afs_vs_fsm(label, pb, dofs, 6, 0.035, 240, 16, warm, extra={"paper_nc": {"fsm": 240, "afs": 61}})
 
 
+def workload_large(n_freq=8):
+    """The large porous solid: a 2 x 1 x 1 m block with 200 seeded spherical voids (radii 0.05-0.1
+    m, level-2 icospheres) and 84 x 42 x 42 face grids, 99280 triangles (297840 complex unknowns);
+    step traction 1e6 Pa on z = 0, z = 1 fixed.  One batched mixed-precision solve (tol 1e-6,
+    GMRES(100)) of the first n_freq frequencies s_k = eta + i k 2 pi / P with P = 40 ms and eta =
+    3 ln(10) / P (Sec. 2.2, kappa = 3) through bem_solve_frequencies.  Prints one JSON line with
+    solves/s, GMRES iterations, refinements and the device memory the solve held."""
+    import torch
+
+    import paper_1511_04355_gb300 as P
+
+    pb = W.porous_block(L=(2.0, 1.0, 1.0), n=(84, 42, 42), n_voids=200, radii=(0.05, 0.1), void_level=2)
+    v, f, m = pb["verts"], pb["tris"], pb["material"]
+    period = 2 * T_WIN
+    eta = 3.0 * math.log(10.0) / period
+    s = eta + 1j * np.arange(n_freq) * 2.0 * math.pi / period
+    c = P.Context(0)
+    t0 = time.perf_counter()
+    c.set_mesh(v, f)
+    c.set_material(m.mu, m.nu, m.rho)
+    c.set_bc(pb["bc_type"], pb["bc_value"], P.BEM_PROFILE_STEP)
+    t_setup = time.perf_counter() - t0
+    c.set_options(precision=P.BEM_PREC_MIXED, tol=TOL, restart=100, max_iters=3000, max_refine=12)
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    free0, total = torch.cuda.mem_get_info()
+    x = torch.zeros((n_freq, 3 * len(f)), dtype=torch.complex128, device="cuda")
+    c.profile(True)
+    t0 = time.perf_counter()
+    _, info = P.bem_solve_frequencies(c.h, torch.from_numpy(s).cuda(), x, allow_not_converged=True)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    kt = c.kernel_times()
+    free1, _ = torch.cuda.mem_get_info()
+    ne = len(f)
+    n32, ms32, fl32 = kt["far32"]
+    line = {"workload": f"porous block 2x1x1 m, 200 voids, {ne} triangles ({3 * ne} complex unknowns), step "
+                        f"traction on z=0, z=1 fixed; {n_freq} frequencies eta + i k 2 pi / {period}",
+            "triangles": ne, "unknowns": 3 * ne, "frequencies": n_freq, "eta": eta,
+            "seconds_setup": t_setup, "seconds_solve": t_solve, "solves_per_s": n_freq / t_solve,
+            "status": info["status"].tolist(), "residual": info["residual"].tolist(),
+            "gmres_iterations": info["iterations"].tolist(), "refinements": info["refinements"].tolist(),
+            "device_bytes_in_use_after_solve": int(total - free1),
+            "far32": {"launches": n32, "ms": ms32,
+                      "tflops_executed": fl32 * ne * (ne - 1) * 4 * FLOPS_EXEC_PER_UNIT_FAR32 / (ms32 / 1e3) / 1e12
+                      if ms32 > 0 else None},
+            "kernel_ms": {k: v[1] for k, v in kt.items()}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -706,7 +755,7 @@ def main():
     ap.add_argument("--profile-step", action="store_true",
                     help="run one benchmark solve with kernel counts (for ncu instruction counters)")
     ap.add_argument("--workload", choices=["uneven", "porous-afs", "porous-afs-full", "example3",
-                                           "example3-mlp"],
+                                           "example3-mlp", "large"],
                     help="run one of the other workloads instead of the benchmark (own JSON line)")
     args = ap.parse_args()
     if args.kernel_case:
@@ -720,6 +769,9 @@ def main():
         return
     if args.workload in ("porous-afs", "porous-afs-full"):
         workload_porous_afs(full=args.workload == "porous-afs-full")
+        return
+    if args.workload == "large":
+        workload_large()
         return
     if args.workload in ("example3", "example3-mlp"):
         workload_example3(warm=2 if args.workload == "example3-mlp" else 0)

@@ -664,11 +664,16 @@ def bem_measure_peak(ctx, kind, iters=2048, reps=5):
 
 
 class Context:
-    """Owns one bem_ctx (device + stream) and remembers the mesh size."""
+    """Owns one bem_ctx (device + stream) and remembers the mesh size.  tuning: a launch-shape
+    table file to load (True: the table written by paper_1511_04355_gb300.tune, when it exists;
+    False: the fixed launch shape)."""
 
-    def __init__(self, device: int = 0, stream=None):
+    def __init__(self, device: int = 0, stream=None, tuning=True):
         self.h = bem_create(device, stream)
         self.ne = 0
+        path = TUNING_TABLE if tuning is True else tuning
+        if path and os.path.exists(path):
+            bem_load_tuning(self.h, path)
 
     def close(self):
         if self.h:

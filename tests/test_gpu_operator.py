@@ -5,8 +5,9 @@ Sizes: 80 and 320 triangles (ragged against the 128-target and 64/32-source tile
 frequencies (ragged against the 12- and 4-frequency tiles) including s = sigma (|z| small, the
 series branch) and the top of the benchmark band; traction-given and mixed boundary conditions.
 Tolerances: FP64 path 1e-10 relative (the two sides differ only in rounding order and in the
-|z| threshold of the Taylor branch); FP32 operator 2e-5 relative in the 2-norm (single-precision
-phase and geometry: |phase| up to ~30 rad carries ~2e-6 absolute error).
+|z| threshold of the Taylor branch); FP32 operator 2e-6 elementwise against the largest entry
+(float-float distances and phases, single-precision kernel algebra), the bound the benchmark-size
+test uses.
 """
 import functools
 
@@ -50,10 +51,6 @@ def _ctx(level, mixed_bc):
     c.set_material(m.mu, m.nu, m.rho)
     c.set_bc(bc, val, P.BEM_PROFILE_STEP)
     return c
-
-
-def _rel(a, b):
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
 @pytest.mark.parametrize("level", [1, 2])
@@ -103,8 +100,12 @@ def test_apply_fp64_and_fp32(level, mixed_bc, which):
     y64 = c.apply(S_SET, x, P.BEM_PREC_FP64, which)
     y32 = c.apply(S_SET, x, P.BEM_PREC_FP32, which)
     for k in range(len(S_SET)):
-        assert np.abs(y64[k] - ref[k]).max() <= 1e-10 * np.abs(ref[k]).max(), k
-        assert _rel(y32[k], ref[k]) < 2e-5, (k, _rel(y32[k], ref[k]))
+        scale = np.abs(ref[k]).max()
+        assert np.abs(y64[k] - ref[k]).max() <= 1e-10 * scale, k
+        # FP32 operator: elementwise, against the largest entry (as at the benchmark size)
+        e32 = np.abs(y32[k] - ref[k]).max() / scale
+        print(f"level {level} mixed {mixed_bc} which {which} k {k}: FP32 elementwise {e32:.2e}")
+        assert e32 < 2e-6, (k, e32)
 
 
 @pytest.mark.parametrize("level,mixed_bc", [(2, False), (1, True)])

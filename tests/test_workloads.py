@@ -72,3 +72,31 @@ def test_porous_block_size_of_the_large_recipe():
     pb = W.porous_block(n=(42, 42, 42), n_voids=27, void_level=2)
     assert len(pb["centres"]) == 27
     assert 25000 < len(pb["tris"]) < 35000
+
+
+def test_example3_block_recipe():
+    """The third example's block: 1 x 1 x 1.5 m, 98 identical cavities of radius 0.072 m inside it,
+    disjoint, fixed on z = 1.5, step traction on z = 0."""
+    pb = W.example3_block(n=(4, 4, 6), void_level=1)
+    v, f, face = pb["verts"], pb["tris"], pb["face"]
+    c, r = pb["centres"], pb["radii"]
+    assert len(c) == 98 and np.allclose(r, 0.072)
+    assert ((c - 0.072 > 0.0) & (c + 0.072 < np.array([1.0, 1.0, 1.5]))).all()
+    d = np.linalg.norm(c[:, None] - c[None], axis=-1) + np.eye(98)
+    assert d.min() > 2 * 0.072
+    # equally spaced layers along z, 14 cavities each
+    assert len(np.unique(np.round(c[:, 2], 9))) == 7
+    assert all((np.round(c[:, 2], 9) == z).sum() == 14 for z in np.unique(np.round(c[:, 2], 9)))
+    assert _closed_and_oriented(f)
+    vol = _signed_volume(v, f)
+    void_vol = sum(-_signed_volume(*W.icosphere(1, 0.072, cc)) for cc in c)
+    assert abs(vol - (1.5 - void_vol)) < 1e-12
+    assert (pb["bc_type"][face == 5] == 1).all() and (pb["bc_type"][face != 5] == 0).all()
+    assert np.allclose(pb["bc_value"][face == 4], [0.0, 0.0, W.CAVITY_P0])
+    assert abs(pb["material"].mu - 69e9 / 2.6) < 1.0 and pb["material"].nu == 0.3
+
+
+def test_large_porous_recipe_size():
+    # the large porous solid: 2 x 1 x 1 m, 200 voids with radii in [0.05, 0.1], ~100000 triangles
+    pb = W.porous_block(L=(2.0, 1.0, 1.0), n=(84, 42, 42), n_voids=200, radii=(0.05, 0.1), void_level=2)
+    assert len(pb["centres"]) == 200 and len(pb["tris"]) == 99280
