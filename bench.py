@@ -637,10 +637,11 @@ def workload_porous_afs(full=False):
     """The porous-block workload: a 1 m block with 27 seeded spherical voids (radii 0.08-0.15 m),
     traction on z = 0, z = 1 fixed; the step response of six unknowns by a 256-frequency FSM and
     by AFS over the same band.  full: the ~30000-triangle recipe (42 x 42 grid per face, level-2
-    voids) over a 40 ms period; else a reduced mesh (20 x 20 per face, level-1 voids, 6960
-    triangles) over a 100 ms period (Omega = 255 pi / 0.05 ~ 16000 rad/s, ~5.5 elements per shear
-    wavelength).  GMRES(200): box problems with a fixed face need hundreds of iterations at the
-    upper frequencies, where GMRES(50) restarts stall."""
+    voids), 256 frequencies over a 40 ms period (Omega ~ 40000 rad/s); else a reduced mesh (20 x
+    20 per face, level-1 voids, 6960 triangles), 128 frequencies over a 50 ms period (Omega =
+    127 x 2 pi / 0.05 ~ 16000 rad/s, ~5.5 elements per shear wavelength).  GMRES(200): box
+    problems with a fixed face need hundreds of iterations at the upper frequencies, where
+    GMRES(50) restarts stall."""
     if full:
         pb = W.porous_block(n=(42, 42, 42), n_voids=27, void_level=2)
     else:
@@ -658,10 +659,10 @@ def workload_porous_afs(full=False):
                      3 * int(voids[0]) + 2, 3 * int(voids[len(voids) // 2]) + 2,
                      3 * nearest(face == 4, [0.25, 0.75, 0.0]) + 2,
                      3 * int(voids[-1]) + 2])
-    period = 2 * T_WIN if full else 0.1
+    period, nc = (2 * T_WIN, 256) if full else (0.05, 128)
     label = (f"porous block 1x1x1 m, 27 voids, {len(f)} triangles ({3 * len(f)} unknowns), step traction "
              "on z=0, z=1 fixed")
-    afs_vs_fsm(label, pb, dofs, 4, period, 256, 8, 0)
+    afs_vs_fsm(label, pb, dofs, 4, period, nc, 8, 0)
 
 
 def workload_example3(warm=0, n=(12, 12, 18), void_level=1):

@@ -500,15 +500,36 @@ void residual_df(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::ve
   for (int t = 0; t < kSeriesDf; ++t) a.m.d[t] = df_split(md.d[t]);
   a.C = make_df_const();
   const int64_t tb = grid_for(a.ne, kTB), groups = grid_for(nfl, kFT);
-  const int64_t want = 4 * 152 * 2;
-  int64_t nsplit = std::max<int64_t>(1, (want + tb * groups - 1) / (tb * groups));
-  nsplit = std::min<int64_t>(nsplit, 65535);
+  const size_t smem = resid_df_smem();
+  BEM_CUDA(cudaFuncSetAttribute(resid_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // Split the sources so that the last wave of CTAs is nearly full: every CTA does the same
+  // work (its share of the sources for its targets and frequencies), so the launch takes
+  // ceil(CTAs / resident slots) CTA-durations, each 1/nsplit of an unsplit CTA, plus a fixed
+  // cost per CTA (set-up and the FP64 atomic adds, counted as one source tile).  The split
+  // minimising that, with chunks of at least 8 source tiles, wins (ties: the smaller split).
+  // Unsplit, 128 frequencies on 5120 triangles made 2.1 waves of which the third ran on a tenth
+  // of the SMs.
+  int per_sm = 0;
+  BEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resid_df_kernel, kTB, smem));
+  const int64_t slots = (int64_t)std::max(per_sm, 1) * (ctx->n_sm > 0 ? ctx->n_sm : 152);
+  const int64_t max_split = std::max<int64_t>(1, std::min<int64_t>(65535, a.ne / (8 * kS)));
+  int64_t nsplit = 1;
+  double best = 1e300;
+  for (int64_t ns = 1; ns <= max_split; ++ns) {
+    int64_t chunk = (a.ne + ns - 1) / ns;
+    chunk = ((chunk + kS - 1) / kS) * kS;
+    const int64_t real_ns = (a.ne + chunk - 1) / chunk;
+    const int64_t waves = (tb * groups * real_ns + slots - 1) / slots;
+    const double cost = (double)waves * (double)(chunk + kS);  // CTA-durations x (sources + overhead)
+    if (cost < best * (1.0 - 1e-9)) {
+      best = cost;
+      nsplit = real_ns;
+    }
+  }
   int64_t chunk = (a.ne + nsplit - 1) / nsplit;
   chunk = ((chunk + kS - 1) / kS) * kS;
   nsplit = (a.ne + chunk - 1) / chunk;
   a.chunk = chunk;
-  const size_t smem = resid_df_smem();
-  BEM_CUDA(cudaFuncSetAttribute(resid_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
     ProfScope ps(ctx, PK_RES64, nfl);
     resid_df_kernel<<<dim3((unsigned)tb, (unsigned)groups, (unsigned)nsplit), kTB, smem, ctx->stream>>>(a);
