@@ -575,14 +575,21 @@ def workload_uneven():
     print(json.dumps(line), flush=True)
 
 
-def afs_vs_fsm(label, pb, dofs, n_orf, period, nc, J0, warm, restart=200, extra=None):
+AFS_TOL = 1e-8   # residual tolerance of the AFS samples (see afs_vs_fsm)
+
+
+def afs_vs_fsm(label, pb, dofs, n_orf, period, nc, J0, warm, restart=200, extra=None, max_samples=None):
     """AFS (Sec. 3) against the FSM (Sec. 2.2) on one problem through the library: the FSM solves
     the nc frequencies eta + i k 2 pi / period at once; AFS samples the same band [0, Omega],
     Omega = (nc - 1) 2 pi / period, adaptively, with its first n_orf unknowns as observation
     responses and the rest as test unknowns.  eta = 3 ln(10) / period (Sec. 2.2 with the kappa =
     3 of Sec. 4).  The transients are compared over the first half of the period, against the
     FSM with the Hanning window (the paper's) and without it (the same band-limited information
-    as the fit: the window smooths what the truncated band leaves).  Prints one JSON line."""
+    as the fit: the window smooths what the truncated band leaves).  The FSM's solves stop at
+    the benchmark tolerance (its result is linear in the samples); AFS's samples are solved to
+    AFS_TOL: vector fits of order J / 2 on samples carrying 1e-6 relative noise keep E1 above
+    its threshold on finite bodies (measured: the 6960-triangle block reached its 128-sample cap
+    with E1 = 2.5e-3).  Prints one JSON line."""
     import paper_1511_04355_gb300 as P
 
     v, f, m = pb["verts"], pb["tris"], pb["material"]
@@ -605,9 +612,9 @@ def afs_vs_fsm(label, pb, dofs, n_orf, period, nc, J0, warm, restart=200, extra=
     del x
     print(json.dumps({"label": label, "fsm_seconds": t_fsm, "triangles": len(f),
                       "fsm_iterations": int(finfo["iterations"].sum())}), file=sys.stderr, flush=True)
-    c.set_options(precision=P.BEM_PREC_MIXED, tol=TOL, restart=restart, max_iters=6000, max_refine=20,
+    c.set_options(precision=P.BEM_PREC_MIXED, tol=AFS_TOL, restart=restart, max_iters=6000, max_refine=20,
                   warm_start=warm)
-    prm = P.bem_default_afs_params(eta=eta, omega_max=omega, T=period, J0=J0, max_samples=nc)
+    prm = P.bem_default_afs_params(eta=eta, omega_max=omega, T=period, J0=J0, max_samples=max_samples or nc)
     t0 = time.perf_counter()
     afs_out, info = c.afs(prm, dofs[:n_orf], dofs[n_orf:], t)
     t_afs = time.perf_counter() - t0
@@ -618,7 +625,9 @@ def afs_vs_fsm(label, pb, dofs, n_orf, period, nc, J0, warm, restart=200, extra=
     line = {"workload": label, "triangles": len(f), "unknowns": 3 * len(f),
             "eta": eta, "period": period, "omega_max": omega,
             "fsm": {"n_c": nc, "seconds": t_fsm, "gmres_iterations": int(finfo["iterations"].sum())},
+            "fsm_tol": TOL, "afs_tol": AFS_TOL,
             "afs": {"n_c": int(info["n_samples"]), "seconds": t_afs, "poles": len(info["poles"]),
+                    "converged": bool(int(info["n_samples"]) < (max_samples or nc)),
                     "E1": float(info["E1"][-1]), "E2": float(info["E2"][-1]),
                     "seconds_solve": info["seconds_solve"], "seconds_fit": info["seconds_fit"],
                     "seconds_train": info["seconds_train"],
@@ -662,7 +671,7 @@ def workload_porous_afs(full=False):
     period, nc = (2 * T_WIN, 256) if full else (0.05, 128)
     label = (f"porous block 1x1x1 m, 27 voids, {len(f)} triangles ({3 * len(f)} unknowns), step traction "
              "on z=0, z=1 fixed")
-    afs_vs_fsm(label, pb, dofs, 4, period, nc, 8, 0)
+    afs_vs_fsm(label, pb, dofs, 4, period, nc, 8, 1, max_samples=nc + nc // 2)
 
 
 def workload_example3(warm=0, n=(12, 12, 18), void_level=1):
@@ -691,7 +700,8 @@ def workload_example3(warm=0, n=(12, 12, 18), void_level=1):
                      3 * nearest(face == 5, [0.6, 0.8, 1.5]) + 2])       # test: t_z, fixed face
     label = (f"block 1x1x1.5 m with 98 cavities r=0.072 m (Example 3), aluminium, {len(f)} triangles "
              f"({3 * len(f)} unknowns), fixed z=1.5, step traction on z=0")
-    afs_vs_fsm(label, pb, dofs, 6, 0.035, 240, 16, warm, extra={"paper_nc": {"fsm": 240, "afs": 61}})
+    afs_vs_fsm(label, pb, dofs, 6, 0.035, 240, 16, warm, extra={"paper_nc": {"fsm": 240, "afs": 61}},
+               max_samples=320)
 
 
 def workload_large(n_freq=8):
@@ -775,7 +785,7 @@ def main():
         workload_large()
         return
     if args.workload in ("example3", "example3-mlp"):
-        workload_example3(warm=2 if args.workload == "example3-mlp" else 0)
+        workload_example3(warm=2 if args.workload == "example3-mlp" else 1)
         return
     if args.warmup < 3:
         args.warmup = 3

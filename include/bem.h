@@ -66,7 +66,8 @@ extern "C" {
 
 #define BEM_WARM_ZERO 0     /* GMRES starts from x0 = 0                                       */
 #define BEM_WARM_NEAREST 1  /* x0 = alpha * the stored solution at the nearest frequency     */
-#define BEM_WARM_MLP 2      /* x0 = alpha * POD basis * MLP(s) (trained by bem_warm_train)   */
+#define BEM_WARM_MLP 2      /* x0 = a1 POD basis MLP(s) + a2 nearest stored solution, (a1, a2)
+                               minimising |b - A x0| (network trained by bem_warm_train)       */
 
 typedef struct bem_ctx bem_ctx;
 
@@ -231,8 +232,11 @@ const char* bem_noalloc_last_error(void);
  * coefficient vectors Phi^H x (unit norm, leading entry real and non-negative); its dense layers
  * run on the tensor cores (FP16 operands, FP32 accumulation), the rest in FP32.  The solve then
  * scales the direction by the complex alpha minimising |b - alpha A x^| (one operator product,
- * which also gives the initial residual), so |r0| <= |b|.  The GMRES tolerance is unchanged:
- * the warm start changes the iteration count, never the accepted accuracy. */
+ * which also gives the initial residual), so |r0| <= |b|.  BEM_WARM_MLP combines the learned
+ * direction with the nearest stored solution: x0 = a1 x^_MLP + a2 x^_nearest with the (a1, a2)
+ * minimising |b - A x0| (two operator products), never worse than either direction alone.  The
+ * GMRES tolerance is unchanged: the warm start changes the iteration count, never the accepted
+ * accuracy. */
 typedef struct bem_warm_params {
   int32_t r_max;    /* POD rank cap (32)                                               */
   double energy_tol; /* POD energy cut: drop modes holding <= energy_tol of sum sigma^2 (1e-10) */
@@ -331,8 +335,8 @@ typedef struct bem_afs_stats {
   double seconds_solve, seconds_fit; /* out: time in BEM solves / in fitting             */
   double seconds_train;     /* out: time spent training the warm-start network            */
   int32_t warm_trainings;   /* out: trainings of the warm-start network                   */
-  int32_t warm_nearest_picks; /* out: learned-start solves that fell back to the nearest
-                               stored solution (smaller initial residual)                 */
+  int32_t warm_learned_gains; /* out: learned-start solves whose combined start left an initial
+                               residual at least 10 % below the nearest stored solution's alone */
 } bem_afs_stats;
 
 /* Fill *p with the paper's parameter values (Sec. 3.4) and the defaults above; eta,
@@ -348,8 +352,8 @@ int bem_default_afs_params(bem_afs_params* p);
  * first clears the warm-start memory, then stores every solution it computes (up to 256) and so
  * starts each new frequency's GMRES from the solutions already sampled; with BEM_WARM_MLP it
  * trains the network (default bem_warm_params) after the initial frequencies and again every
- * params->warm_retrain new samples, and falls back per frequency to the nearest stored solution
- * when that leaves the smaller initial residual.  The GMRES tolerance is unchanged. 
+ * params->warm_retrain new samples; each learned start is combined with the nearest stored
+ * solution (see BEM_WARM_MLP).  The GMRES tolerance is unchanged. 
  * resp_out[nt_out x (K + Kt)] (host or device): time responses of the ORFs then the test
  * unknowns at t_out[nt_out] (Eq. (vf-td), final fit); stats nullable.
  * Errors: INVALID_ARG, NOT_CONVERGED (a frequency solve failed), NO_MESH, CUDA. */

@@ -86,7 +86,7 @@ class bem_afs_stats(C.Structure):
                 ("n_samples", C.c_int64), ("n_steps", C.c_int64), ("n_poles", C.c_int32),
                 ("seconds_solve", C.c_double), ("seconds_fit", C.c_double),
                 ("seconds_train", C.c_double), ("warm_trainings", C.c_int32),
-                ("warm_nearest_picks", C.c_int32)]
+                ("warm_learned_gains", C.c_int32)]
 
 
 class bem_warm_params(C.Structure):
@@ -540,7 +540,7 @@ def bem_afs(ctx, params, orf, test, t_out, capacity=1024):
                 E2=arr["E2"][:ns], poles=arr["poles"][:npol], n_samples=n,
                 seconds_solve=st.seconds_solve, seconds_fit=st.seconds_fit,
                 seconds_train=st.seconds_train, warm_trainings=st.warm_trainings,
-                warm_nearest_picks=st.warm_nearest_picks)
+                warm_learned_gains=st.warm_learned_gains)
     return out, info
 
 

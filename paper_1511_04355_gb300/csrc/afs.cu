@@ -222,7 +222,7 @@ int bem_afs(bem_ctx* ctx, const bem_afs_params* prm, const int64_t* orf, int64_t
     const int retrain = p.warm_retrain > 0 ? p.warm_retrain : 4;
     constexpr int kWarmCap = 256;  // solutions the network can be trained on
     int warm_trainings = 0, last_train = 0;
-    int64_t nearest_picks = 0;
+    int64_t learned_gains = 0;
     if (wmode != BEM_WARM_ZERO) {
       ctx->warm.s.clear();
       ctx->warm.trained = false;
@@ -253,7 +253,7 @@ int bem_afs(bem_ctx* ctx, const bem_afs_params* prm, const int64_t* orf, int64_t
       Fout.resize(F * nobs);
       for (int64_t q = 0; q < F * nobs; ++q) Fout[q] = cd(h[q].r, h[q].i);
       for (int64_t f = 0; f < F; ++f) solve_iters.push_back(it[f]);
-      nearest_picks += ctx->warm_nearest_picks;
+      learned_gains += ctx->warm_learned_gains;
       if (wmode != BEM_WARM_ZERO) {
         const int64_t room = kWarmCap - (int64_t)ctx->warm.s.size() / 2;
         if (room > 0) warm_store(ctx, sr.data(), std::min(F, room), ctx->io_a.as<cx<double>>());
@@ -355,7 +355,7 @@ int bem_afs(bem_ctx* ctx, const bem_afs_params* prm, const int64_t* orf, int64_t
       st->seconds_fit = t_fit;
       st->seconds_train = t_train;
       st->warm_trainings = warm_trainings;
-      st->warm_nearest_picks = (int32_t)nearest_picks;
+      st->warm_learned_gains = (int32_t)learned_gains;
       const int64_t cap = st->capacity;
       for (int64_t j = 0; j < (int64_t)s.size() && j < cap; ++j) {
         if (st->s) {

@@ -277,8 +277,8 @@ struct bem_ctx {
   bool tune_forced = false;          // the autotuner's trial shape overrides the table
   bem::FarShape tune_force;
   int n_sm = 0;                      // multiprocessors of the device
-  int64_t warm_nearest_picks = 0; // frequencies of the last solve whose learned start fell back
-                                  // to the nearest stored solution
+  int64_t warm_learned_gains = 0; // frequencies of the last solve whose learned start, combined with
+                                  // the nearest solution, beat that solution alone by >= 10 %
   // kernel timing
   bool prof = false;
   std::vector<bem::ProfRec> prof_recs;

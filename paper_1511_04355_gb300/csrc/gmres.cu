@@ -286,6 +286,80 @@ __global__ void warm_scale_kernel(const cx<double>* b, const cx<Ry>* y, cx<doubl
   }
 }
 
+// Two-direction warm start, one block per frequency f: x0 = a1 x1 + a2 x2 with the complex
+// (a1, a2) minimising |b - a1 y1 - a2 y2| (y_j = A x_j), by the 2 x 2 normal equations; when the
+// directions are nearly parallel (Gram determinant below 1e-10 of its scale) the better single
+// direction is used.  x1 is overwritten by x0, r = b - a1 y1 - a2 y2 (r may alias b).  Also
+// writes the squared residuals of the combination and of x2 alone (rn2[2 f], rn2[2 f + 1]).
+template <class Ry>
+__global__ void warm_combine_kernel(const cx<double>* b, const cx<Ry>* y1, const cx<Ry>* y2, cx<double>* x1,
+                                    const cx<double>* x2, cx<double>* r, int64_t N, double* rn2) {
+  constexpr int NT = 256;
+  __shared__ double sm[9][NT];
+  const int64_t f = blockIdx.x;
+  const cx<double>* bf = b + f * N;
+  const cx<Ry>* p = y1 + f * N;
+  const cx<Ry>* q = y2 + f * N;
+  double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // g11 g22 g12(r,i) c1(r,i) c2(r,i) bb
+  for (int64_t n = threadIdx.x; n < N; n += NT) {
+    const cx<double> bv = bf[n];
+    const double pr = (double)p[n].r, pi = (double)p[n].i, qr = (double)q[n].r, qi = (double)q[n].i;
+    acc[0] += pr * pr + pi * pi;
+    acc[1] += qr * qr + qi * qi;
+    acc[2] += pr * qr + pi * qi;          // conj(y1) y2
+    acc[3] += pr * qi - pi * qr;
+    acc[4] += pr * bv.r + pi * bv.i;      // conj(y1) b
+    acc[5] += pr * bv.i - pi * bv.r;
+    acc[6] += qr * bv.r + qi * bv.i;      // conj(y2) b
+    acc[7] += qr * bv.i - qi * bv.r;
+    acc[8] += bv.r * bv.r + bv.i * bv.i;
+  }
+  for (int k = 0; k < 9; ++k) sm[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int h = NT / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+      for (int k = 0; k < 9; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + h];
+    __syncthreads();
+  }
+  const double g11 = sm[0][0], g22 = sm[1][0], bb = sm[8][0];
+  const cx<double> g12 = mk(sm[2][0], sm[3][0]), c1 = mk(sm[4][0], sm[5][0]), c2 = mk(sm[6][0], sm[7][0]);
+  const double det = g11 * g22 - (g12.r * g12.r + g12.i * g12.i);
+  cx<double> a1 = mk(0.0, 0.0), a2 = mk(0.0, 0.0);
+  double res2;
+  // x2 alone (the nearest stored solution)
+  const double near2 = g22 > 0 ? bb - (c2.r * c2.r + c2.i * c2.i) / g22 : bb;
+  if (g11 > 0 && g22 > 0 && det > 1e-10 * g11 * g22) {
+    // [g11 g12; conj(g12) g22] [a1; a2] = [c1; c2]
+    const cx<double> n1 = g22 * c1 - g12 * c2;
+    const cx<double> n2 = g11 * c2 - conj(g12) * c1;
+    a1 = mk(n1.r / det, n1.i / det);
+    a2 = mk(n2.r / det, n2.i / det);
+    res2 = bb - ((conj(c1) * a1).r + (conj(c2) * a2).r);
+  } else {
+    const double one2 = g11 > 0 ? bb - (c1.r * c1.r + c1.i * c1.i) / g11 : bb;
+    if (g11 > 0 && one2 <= near2) {
+      a1 = mk(c1.r / g11, c1.i / g11);
+      res2 = one2;
+    } else {
+      if (g22 > 0) a2 = mk(c2.r / g22, c2.i / g22);
+      res2 = near2;
+    }
+  }
+  if (threadIdx.x == 0) {
+    rn2[2 * f] = res2;
+    rn2[2 * f + 1] = near2;
+  }
+  cx<double>* xf = x1 + f * N;
+  const cx<double>* xn = x2 + f * N;
+  cx<double>* rf = r + f * N;
+  for (int64_t n = threadIdx.x; n < N; n += NT) {
+    const cx<double> yv1 = mk((double)p[n].r, (double)p[n].i), yv2 = mk((double)q[n].r, (double)q[n].i);
+    const cx<double> bv = bf[n];
+    xf[n] = a1 * xf[n] + a2 * xn[n];
+    rf[n] = bv - a1 * yv1 - a2 * yv2;
+  }
+}
+
 // r = b - Ax  (for active instances)
 __global__ void residual_kernel(const cx<double>* b, const cx<double>* Ax, cx<double>* r,
                                 int64_t N, int64_t F, const int32_t* act) {
@@ -479,12 +553,11 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
   }
   const bool warm = o.warm_start != BEM_WARM_ZERO && ctx->warm.N == N && !ctx->warm.s.empty() &&
                     (o.warm_start == BEM_WARM_NEAREST || ctx->warm.trained);
-  ctx->warm_nearest_picks = 0;
+  ctx->warm_learned_gains = 0;
   if (warm) {
     // direction x^ from the warm start, y = A x^ with the operator of the inner solve's
-    // precision, then x0 = alpha x^ and r = b - alpha y with the alpha minimising |r|.  With the
-    // learned start, the nearest stored solution is the fallback: both candidates are scaled and
-    // each frequency keeps the one with the smaller initial residual.
+    // precision, then x0 = alpha x^ and r = b - alpha y with the alpha minimising |r|.  The
+    // learned start combines its direction with the nearest stored solution (see below).
     const cx<double>* bsrc = mixed ? W.r.as<cx<double>>() : W.b.as<cx<double>>();
     auto candidate = [&](int mode, cx<double>* x, cx<double>* r, double* rn2) {
       warm_initial(ctx, mode, ctx->fs.s.data(), F, x);
@@ -506,28 +579,48 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
     };
     DevBuf r1;
     r1.reserve(sizeof(cx<double>) * F * N);
-    candidate(o.warm_start, x_dev, r1.as<cx<double>>(), W.rn2.as<double>());
     if (o.warm_start == BEM_WARM_MLP) {
-      DevBuf x2, r2, n2;
+      // learned direction x1 = Phi c(s) and nearest stored solution x2, combined as
+      // x0 = a1 x1 + a2 x2 with the (a1, a2) minimising |b - A x0|: never worse than either alone
+      DevBuf x2, rr;
       x2.reserve(sizeof(cx<double>) * F * N);
-      r2.reserve(sizeof(cx<double>) * F * N);
-      n2.reserve(sizeof(double) * F);
-      candidate(BEM_WARM_NEAREST, x2.as<cx<double>>(), r2.as<cx<double>>(), n2.as<double>());
-      std::vector<double> a1(F), a2(F);
-      BEM_CUDA(cudaMemcpyAsync(a1.data(), W.rn2.p, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
-      BEM_CUDA(cudaMemcpyAsync(a2.data(), n2.p, sizeof(double) * F, cudaMemcpyDeviceToHost, st));
-      BEM_CUDA(cudaStreamSynchronize(st));
-      for (int64_t f = 0; f < F; ++f) {
-        if (!(a2[f] < a1[f])) continue;
-        BEM_CUDA(cudaMemcpyAsync(x_dev + f * N, x2.as<cx<double>>() + f * N, sizeof(cx<double>) * N,
-                                 cudaMemcpyDeviceToDevice, st));
-        BEM_CUDA(cudaMemcpyAsync(r1.as<cx<double>>() + f * N, r2.as<cx<double>>() + f * N,
-                                 sizeof(cx<double>) * N, cudaMemcpyDeviceToDevice, st));
-        BEM_CUDA(cudaMemcpyAsync(W.rn2.as<double>() + f, n2.as<double>() + f, sizeof(double),
-                                 cudaMemcpyDeviceToDevice, st));
-        ctx->warm_nearest_picks++;
+      rr.reserve(sizeof(double) * 2 * F);
+      warm_initial(ctx, BEM_WARM_MLP, ctx->fs.s.data(), F, x_dev);
+      warm_initial(ctx, BEM_WARM_NEAREST, ctx->fs.s.data(), F, x2.as<cx<double>>());
+      if (mixed) {
+        DevBuf xf, y1, y2;
+        xf.reserve(sizeof(cx<float>) * F * N);
+        y1.reserve(sizeof(cx<float>) * F * N);
+        y2.reserve(sizeof(cx<float>) * F * N);
+        narrow_array(ctx, x_dev, xf.as<cx<float>>(), F * N);
+        apply_operator32(ctx, xf.as<cx<float>>(), y1.as<cx<float>>(), BEM_APPLY_A, nullptr);
+        narrow_array(ctx, x2.as<cx<double>>(), xf.as<cx<float>>(), F * N);
+        apply_operator32(ctx, xf.as<cx<float>>(), y2.as<cx<float>>(), BEM_APPLY_A, nullptr);
+        warm_combine_kernel<float><<<(unsigned)F, 256, 0, st>>>(bsrc, y1.as<cx<float>>(), y2.as<cx<float>>(), x_dev,
+                                                                x2.as<cx<double>>(), r1.as<cx<double>>(), N,
+                                                                rr.as<double>());
+        BEM_LAUNCHED();
+        BEM_CUDA(cudaStreamSynchronize(st));
+      } else {
+        DevBuf y2;
+        y2.reserve(sizeof(cx<double>) * F * N);
+        apply_operator64(ctx, x_dev, W.Ax.as<cx<double>>(), BEM_APPLY_A, nullptr);
+        apply_operator64(ctx, x2.as<cx<double>>(), y2.as<cx<double>>(), BEM_APPLY_A, nullptr);
+        warm_combine_kernel<double><<<(unsigned)F, 256, 0, st>>>(bsrc, W.Ax.as<cx<double>>(), y2.as<cx<double>>(),
+                                                                 x_dev, x2.as<cx<double>>(), r1.as<cx<double>>(), N,
+                                                                 rr.as<double>());
+        BEM_LAUNCHED();
+        BEM_CUDA(cudaStreamSynchronize(st));
       }
-      BEM_CUDA(cudaStreamSynchronize(st));  // x2, r2, n2 are freed on return from this block
+      ctx->launches++;
+      std::vector<double> rh(2 * F);
+      BEM_CUDA(cudaMemcpy(rh.data(), rr.p, sizeof(double) * 2 * F, cudaMemcpyDeviceToHost));
+      for (int64_t f = 0; f < F; ++f)
+        if (rh[2 * f] < 0.81 * rh[2 * f + 1]) ctx->warm_learned_gains++;  // residual >= 10 % lower
+      norm2_kernel<double><<<(unsigned)F, 256, 0, st>>>(r1.as<cx<double>>(), N, nullptr, W.rn2.as<double>());
+      ctx->launches++;
+    } else {
+      candidate(o.warm_start, x_dev, r1.as<cx<double>>(), W.rn2.as<double>());
     }
     BEM_CUDA(cudaMemcpyAsync(W.r.p, r1.p, sizeof(cx<double>) * F * N, cudaMemcpyDeviceToDevice, st));
     BEM_CUDA(cudaStreamSynchronize(st));

@@ -3,7 +3,8 @@ next to the frequencies already solved), through bem_afs.
 
 For each workload bem_afs runs three times, with the context's warm_start set to ZERO (GMRES
 from x0 = 0), NEAREST (the stored solution at the nearest sampled frequency) and MLP (the POD +
-MLP prediction, retrained every 4 samples, the nearest solution as the per-frequency fallback).
+MLP prediction, retrained every 4 samples, combined with the nearest solution by minimal
+residual).
 The warm start may change the GMRES iterations only: every run must sample the same number of
 frequencies (within 2, since the greedy choice can take another branch on rounding-level
 differences of the solutions) and return the same transients (within 2e-3 of the largest
@@ -80,7 +81,8 @@ def test_afs_warm_start_modes(case):
         print(f"{case} {name}: N_c {info['n_samples']}, GMRES iterations initial {int(it[:J0].sum())} "
               f"adaptive {int(it[J0:].sum())} (mean {it[J0:].mean():.1f}), solve {info['seconds_solve']:.2f} s, "
               f"fit {info['seconds_fit']:.2f} s, train {info['seconds_train']:.2f} s "
-              f"({info['warm_trainings']} trainings, {info['warm_nearest_picks']} nearest fallbacks)")
+              f"({info['warm_trainings']} trainings, {info['warm_learned_gains']} solves where the network's "
+              f"direction helped)")
         print(f"{case} {name} per-solve iterations: {it.tolist()}")
         assert info["E1"][-1] < prm.get("E1bar", 1e-4) and info["E2"][-1] < 2e-3
         assert info["n_samples"] < prm["max_samples"]
