@@ -10,9 +10,11 @@ FP64, FP32 matrix-free operator with FP64 iterative refinement.
 value : solves/s with the frequency list, the mesh and the output already in device memory.
 e2e   : the same through the C ABI with host buffers (mesh, boundary data and frequencies
         uploaded, all solutions downloaded, every step).
-Also reported: the plain-FP64 GPU path on a 16-frequency sample, the per-kernel roofline of the
-dominant kernel (CUDA events around each launch on the launching stream), SM clocks sampled
-during the timed region, and the FP64 CPU oracle on a bounded sample (cpu_baseline).
+Also reported: the plain-FP64 GPU path on all 128 frequencies; the accuracy of the timed
+solutions and of a tol-2e-7 solve against a tol-1e-9 one (elementwise and in the FSM transients);
+the per-kernel rooflines (executed flops over CUDA-event times of each launch on the launching
+stream, against FP32 / FP64 peaks measured in the same run); SM clocks sampled during the timed
+region; and the FP64 CPU oracle on a bounded sample (cpu_baseline).
 
 --impl reference times the CPU oracle (dense assembly + LU, FP64) on the same workload: each
 step is a bounded sample (a block of matrix rows at one frequency plus an LU of a smaller dense
