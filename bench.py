@@ -60,7 +60,7 @@ FLOPS_PER_UNIT_RES = 221  # fused FP64 residual r = K k - A x: T and U per kerne
 # The same residual in float-float on the FP32 pipes (resid_df_kernel, lazily renormalised
 # pairs): FP32 flops per kernel evaluation, FADD + FMUL + 2 FFMA thread-instructions of one launch
 # (ncu executed-instruction counters, 24 frequencies on 5120 triangles) divided by its units
-FLOPS_PER_UNIT_RES_DF = 1802
+FLOPS_PER_UNIT_RES_DF = 1537.5  # FADD 749.4 + FMUL 135.3 + 2 x FFMA 326.6 per unit
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0  # nominal, for the derived-peak note only
 # Executed flops per kernel evaluation of the far-field kernels (FADD + FMUL + 2 FFMA, resp.
 # DADD + DMUL + 2 DFMA thread instructions from ncu executed-instruction counters divided by the
@@ -528,6 +528,7 @@ def profile_step():
     n32, ms32, fl32 = kt["far32"]
     print(json.dumps({"far32_launches": n32, "far32_freq_launches": fl32,
                       "far32_units": fl32 * ne * (ne - 1) * 4, "far32_ms": ms32,
+                      "kernel_ms": {k: v[1] for k, v in kt.items()},
                       "gmres_iterations": int(info["iterations"].sum())}))
 
 

@@ -89,6 +89,43 @@ __device__ __forceinline__ void point_terms(cdf Es, cdf Ep, cdf zs, cdf zp, df i
   oc[2] = cadd(cadd(cmul(t1, v[2]), cmul(psi, v[6])), cadd(cscale(n2, t2), cscale(rz, t3p)));
 }
 
+// The same point algebra split for a per-element application: oc[c] = rh_c t3' (the part that
+// depends on the point's direction), and the scalars that multiply the element's own vectors,
+// sc = (t1, psi, t2) with  point contribution_c = t1 vT_c + psi vU_c + n_c t2 + oc[c].  Summing
+// sc over the element's points and applying it once per element replaces, per point, six
+// complex float-float products and three scalings by three additions.
+__device__ __forceinline__ void point_terms_split(cdf Es, cdf Ep, cdf zs, cdf zp, df inv_r2, const FreqDf& F,
+                                                  const MatDf& m, df cw, df cwd, df cu, df drdn, df rx, df ry,
+                                                  df rz, const cdf* v, cdf* oc, cdf* sc) {
+  const cdf gs = cadd(Es, cmul(zs, Es));
+  const cdf gp = cadd(Ep, cmul(zp, Ep));
+  const cdf Pp = csub(Es, cscale(m.beta2, Ep));
+  cdf J;
+  if (zs.r.h * zs.r.h + zs.i.h * zs.i.h < kZSeriesDf2) {
+    J = cmk(m.d[kSeriesDf - 1], dfm(0.f, 0.f));
+#pragma unroll 1
+    for (int t = kSeriesDf - 2; t >= 0; --t) J = cadd(cmul(J, zs), cmk(m.d[t], dfm(0.f, 0.f)));
+  } else {
+    J = cscale(inv_r2, cmul(csub(gp, gs), F.inv_a2));
+  }
+  const cdf Q = csub(cscalef(6.f, J), cmk(scale2(Pp.r, 2.f), scale2(Pp.i, 2.f)));
+  const cdf A = csub(Q, gs);
+  const cdf q1 = csub(Q, cscale(m.c1m2b2, gp));
+  const cdf g2 = csub(gs, cscale(m.beta2, gp));
+  const cdf q2 = csub(cmk(scale2(g2.r, 2.f), scale2(g2.i, 2.f)), cscalef(5.f, Q));
+  const cdf rv = cadd(cadd(cscale(rx, v[0]), cscale(ry, v[1])), cscale(rz, v[2]));
+  const cdf t3 = cscale(cw, cadd(cmul(q1, v[3]), cscale(drdn, cmul(q2, rv))));
+  const cdf ru = cadd(cadd(cscale(rx, v[4]), cscale(ry, v[5])), cscale(rz, v[6]));
+  const cdf crv = cmul(cscale(cu, csub(Pp, cscalef(3.f, J))), ru);
+  const cdf t3p = csub(t3, crv);
+  sc[0] = cscale(cwd, A);                 // t1, multiplies vT_c
+  sc[1] = cscale(cu, csub(Es, J));        // psi, multiplies vU_c
+  sc[2] = cmul(cscale(cw, A), rv);        // t2, multiplies n_c
+  oc[0] = cscale(rx, t3p);
+  oc[1] = cscale(ry, t3p);
+  oc[2] = cscale(rz, t3p);
+}
+
 __global__ void __launch_bounds__(kTB) resid_df_kernel(const ResDfArgs a) {
   constexpr int TB = kTB, S = kS, FT = kFT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -96,7 +133,9 @@ __global__ void __launch_bounds__(kTB) resid_df_kernel(const ResDfArgs a) {
   // frequency loop stays rolled (the float-float body is large; unrolling it overflowed the
   // instruction cache), so its sums live in shared memory rather than in registers
   float* pacc = reinterpret_cast<float*>(smem_raw);                     // [FT * 12][TB]
-  float* sq = pacc + FT * 12 * TB;                                       // [S][4][8]
+  float* psum = pacc + FT * 12 * TB;                                     // [FT * 12][TB]: per-element
+                                                                         // sums of (t1, psi, t2)
+  float* sq = psum + FT * 12 * TB;                                       // [S][4][8]
   float* sn = sq + S * 4 * 8;                                            // [S][8]
   cdf* sv = reinterpret_cast<cdf*>(sn + S * 8);                          // [S][FT][7]
   FreqDf* sfc = reinterpret_cast<FreqDf*>(sv + S * FT * 7);              // [FT]
@@ -217,9 +256,10 @@ __global__ void __launch_bounds__(kTB) resid_df_kernel(const ResDfArgs a) {
           df_sincos(ph_p, C, sn_, cs_);
           const cdf Ep = cmk(mul(Ap, cs_), neg(mul(Ap, sn_)));
           const cdf zs = cmk(zr_s, ph_s), zp = cmk(zr_p, ph_p);
-          cdf oc[3];
-          point_terms(Es, Ep, zs, zp, inv_r2, F, m, cw, cwd, cu, drdn, rx, ry, rz, n0, n1, n2, v, oc);
+          cdf oc[3], sc[3];
+          point_terms_split(Es, Ep, zs, zp, inv_r2, F, m, cw, cwd, cu, drdn, rx, ry, rz, v, oc, sc);
           float* pa = pacc + (k * 12) * TB + tid;
+          float* ps = psum + (k * 12) * TB + tid;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             float* pc = pa + (4 * c) * TB;
@@ -229,7 +269,36 @@ __global__ void __launch_bounds__(kTB) resid_df_kernel(const ResDfArgs a) {
             pc[TB] = re.l;
             pc[2 * TB] = im.h;
             pc[3 * TB] = im.l;
+            float* pt = ps + (4 * c) * TB;
+            const df sr = q == 0 ? sc[c].r : add_n(dfm(pt[0], pt[TB]), sc[c].r);
+            const df si = q == 0 ? sc[c].i : add_n(dfm(pt[2 * TB], pt[3 * TB]), sc[c].i);
+            pt[0] = sr.h;
+            pt[TB] = sr.l;
+            pt[2 * TB] = si.h;
+            pt[3 * TB] = si.l;
           }
+        }
+      }
+      // the element's sums applied once: t1 vT_c + psi vU_c + n_c t2
+#pragma unroll 1
+      for (int k = 0; k < nf; ++k) {
+        const cdf* v = sv + 7 * (e * FT + k);
+        const float* ps = psum + (k * 12) * TB + tid;
+        const cdf S1 = cmk(dfm(ps[0], ps[TB]), dfm(ps[2 * TB], ps[3 * TB]));
+        const cdf S2 = cmk(dfm(ps[4 * TB], ps[5 * TB]), dfm(ps[6 * TB], ps[7 * TB]));
+        const cdf S3 = cmk(dfm(ps[8 * TB], ps[9 * TB]), dfm(ps[10 * TB], ps[11 * TB]));
+        const df nn3[3] = {n0, n1, n2};
+        float* pa = pacc + (k * 12) * TB + tid;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const cdf o = cadd(cadd(cmul(S1, v[c]), cmul(S2, v[4 + c])), cscale(nn3[c], S3));
+          float* pc = pa + (4 * c) * TB;
+          const df re = add_n(dfm(pc[0], pc[TB]), o.r);
+          const df im = add_n(dfm(pc[2 * TB], pc[3 * TB]), o.i);
+          pc[0] = re.h;
+          pc[TB] = re.l;
+          pc[2 * TB] = im.h;
+          pc[3 * TB] = im.l;
         }
       }
     }
@@ -451,7 +520,7 @@ __global__ void __launch_bounds__(128) self_sums_df_kernel(const SelfDfArgs a) {
 }
 
 size_t resid_df_smem() {
-  return sizeof(float) * 12 * kFT * kTB + sizeof(float) * kS * 4 * 8 + sizeof(float) * kS * 8 +
+  return sizeof(float) * 2 * 12 * kFT * kTB + sizeof(float) * kS * 4 * 8 + sizeof(float) * kS * 8 +
          sizeof(cdf) * kS * kFT * 7 + sizeof(FreqDf) * kFT + sizeof(DfConst);
 }
 
