@@ -468,6 +468,7 @@ int bem_launch_shape(bem_ctx* ctx, int64_t nfl, int32_t* ft, int32_t* tiles, int
  * Errors: INVALID_ARG (kind, iters < 1, reps < 1), OOM, CUDA. */
 #define BEM_PEAK_FP32 0
 #define BEM_PEAK_FP64 1
+#define BEM_PEAK_FP32X2 2  /* FP32 with the paired instruction (two FMAs per thread per FFMA2) */
 int bem_measure_peak(bem_ctx* ctx, int kind, int32_t iters, int32_t reps, double* tflops,
                      double* ms_best, int32_t* sm_count);
 

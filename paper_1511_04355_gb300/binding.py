@@ -47,6 +47,7 @@ BEM_KERNEL_VEC = 5
 BEM_KERNEL_RES64 = 6
 BEM_PEAK_FP32 = 0
 BEM_PEAK_FP64 = 1
+BEM_PEAK_FP32X2 = 2
 KERNEL_NAMES = {0: "far32", 1: "far64", 2: "near32", 3: "near64", 4: "self", 5: "gmres_vec",
                 6: "res64"}
 

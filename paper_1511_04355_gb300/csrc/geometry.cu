@@ -424,10 +424,13 @@ __device__ bool inv3(const cx<double>* A, cx<double>* B) {
   return true;
 }
 
-// One warp per (frequency, element): 3 x 169 Duffy points spread over the lanes.
+// One warp per (frequency, element): 3 x 169 Duffy points spread over the lanes.  When the Duffy
+// sums come precomputed (a.sums, float-float), what is left (closed-form CPV, assembly, inverse)
+// is one thread's work: one thread per (frequency, element).
 __global__ void self_blocks_kernel(SelfArgs a) {
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t w = a.sums ? gt : gt >> 5;
+  const int lane = a.sums ? 0 : (int)(threadIdx.x & 31);
   const int64_t nitem = a.idx ? a.F : a.F * a.ne;  // with idx: F = number of listed elements
   if (w >= nitem) return;
   int64_t f, i;
@@ -636,7 +639,6 @@ void prepare_frequencies(bem_ctx* ctx, const double* s, int64_t F, bool df_self)
   a.Minv32 = fs.Minv32.as<cx<float>>();
   a.idx = nullptr;
   a.singular = sing.as<int>();
-  const int64_t threads = 32 * F * me.ne;
   ProfScope ps(ctx, PK_SELF);
   DevBuf sums;
   a.sums = nullptr;
@@ -645,6 +647,7 @@ void prepare_frequencies(bem_ctx* ctx, const double* s, int64_t F, bool df_self)
     self_sums_df(ctx, sums.as<cx<double>>());
     a.sums = sums.as<cx<double>>();
   }
+  const int64_t threads = (df_self ? 1 : 32) * F * me.ne;
   self_blocks_kernel<<<grid_for(threads, 128), 128, 0, ctx->stream>>>(a);
   BEM_LAUNCHED();
   ctx->launches++;

@@ -36,7 +36,27 @@ __global__ void __launch_bounds__(kThreads) fma_chain_kernel(R a, R b, int iters
   if (s == (R)-1.2345e30) sink[blockIdx.x] = s;
 }
 
-template <class R>
+// The same chains with the paired FP32 instruction (two fused multiply-adds per thread and
+// instruction, __ffma2_rn): whether the FP32 pipes run faster per issued instruction.
+__global__ void __launch_bounds__(kThreads) fma2_chain_kernel(float a, float b, int iters, float* sink) {
+  float2 x[kChains / 2];
+#pragma unroll
+  for (int c = 0; c < kChains / 2; ++c) x[c] = make_float2((float)(threadIdx.x + 2 * c) * 1e-3f, (float)(threadIdx.x + 2 * c + 1) * 1e-3f);
+  const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll 16
+    for (int u = 0; u < 16; ++u) {
+#pragma unroll
+      for (int c = 0; c < kChains / 2; ++c) x[c] = __ffma2_rn(x[c], a2, b2);
+    }
+  }
+  float s = 0;
+#pragma unroll
+  for (int c = 0; c < kChains / 2; ++c) s += x[c].x + x[c].y;
+  if (s == -1.2345e30f) sink[blockIdx.x] = s;
+}
+
+template <class R, bool PAIRED = false>
 void measure(bem_ctx* ctx, int iters, int reps, double* tflops, double* ms_best, int32_t* sms) {
   int n_sm = 0;
   BEM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
@@ -50,11 +70,15 @@ void measure(bem_ctx* ctx, int iters, int reps, double* tflops, double* ms_best,
     BEM_CUDA(cudaEventCreate(&e1));
     // a = 1 - 2^-20, b = 2^-20: the chains stay finite and non-constant for any length
     const R a = (R)1 - (R)9.5367431640625e-7, b = (R)9.5367431640625e-7;
-    fma_chain_kernel<R><<<blocks, kThreads, 0, ctx->stream>>>(a, b, iters, sink);  // warm-up
+    auto launch = [&] {
+      if constexpr (PAIRED) fma2_chain_kernel<<<blocks, kThreads, 0, ctx->stream>>>(a, b, iters, sink);
+      else fma_chain_kernel<R><<<blocks, kThreads, 0, ctx->stream>>>(a, b, iters, sink);
+    };
+    launch();  // warm-up
     BEM_LAUNCHED();
     for (int r = 0; r < reps; ++r) {
       BEM_CUDA(cudaEventRecord(e0, ctx->stream));
-      fma_chain_kernel<R><<<blocks, kThreads, 0, ctx->stream>>>(a, b, iters, sink);
+      launch();
       BEM_LAUNCHED();
       BEM_CUDA(cudaEventRecord(e1, ctx->stream));
       BEM_CUDA(cudaEventSynchronize(e1));
@@ -86,10 +110,13 @@ using namespace bem;
 extern "C" int bem_measure_peak(bem_ctx* ctx, int kind, int32_t iters, int32_t reps,
                                 double* tflops, double* ms_best, int32_t* sm_count) {
   return guarded_call(ctx, [&] {
-    BEM_REQUIRE(kind == BEM_PEAK_FP32 || kind == BEM_PEAK_FP64, "kind must be BEM_PEAK_FP32 or BEM_PEAK_FP64");
+    BEM_REQUIRE(kind == BEM_PEAK_FP32 || kind == BEM_PEAK_FP64 || kind == BEM_PEAK_FP32X2,
+                "kind must be BEM_PEAK_FP32, BEM_PEAK_FP64 or BEM_PEAK_FP32X2");
     BEM_REQUIRE(iters >= 1 && reps >= 1, "iters and reps must be >= 1");
     if (kind == BEM_PEAK_FP32)
       measure<float>(ctx, iters, reps, tflops, ms_best, sm_count);
+    else if (kind == BEM_PEAK_FP32X2)
+      measure<float, true>(ctx, iters, reps, tflops, ms_best, sm_count);
     else
       measure<double>(ctx, iters, reps, tflops, ms_best, sm_count);
   });
