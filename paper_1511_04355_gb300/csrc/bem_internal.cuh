@@ -80,33 +80,6 @@ __host__ __device__ __forceinline__ cx<R> cfma(cx<R> b, cx<R> c, cx<R> a) {
   return mk(fma(b.r, c.r, fma(-b.i, c.i, a.r)), fma(b.r, c.i, fma(b.i, c.r, a.i)));
 }
 
-// FP32 complex arithmetic on the paired FP32 instructions of sm_100-family GPUs (FADD2 / FMUL2 /
-// FFMA2: one instruction does the real and the imaginary part), which halves the issue slots of
-// the FP32 kernels' complex algebra.  Same operations as the generic forms above (products,
-// fused multiply-adds and sums, each rounded once), grouped in pairs.  BEM_NO_F32X2 builds the
-// scalar forms instead.
-#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000) && !defined(BEM_NO_F32X2)
-#define BEM_F32X2 1
-__device__ __forceinline__ float2 f2_(cx<float> z) { return make_float2(z.r, z.i); }
-__device__ __forceinline__ cx<float> cf_(float2 v) { return mk(v.x, v.y); }
-__device__ __forceinline__ cx<float> operator+(cx<float> a, cx<float> b) { return cf_(__fadd2_rn(f2_(a), f2_(b))); }
-__device__ __forceinline__ cx<float> operator-(cx<float> a, cx<float> b) {
-  return cf_(__ffma2_rn(make_float2(-1.f, -1.f), f2_(b), f2_(a)));
-}
-__device__ __forceinline__ cx<float> operator*(float a, cx<float> b) { return cf_(__fmul2_rn(make_float2(a, a), f2_(b))); }
-__device__ __forceinline__ cx<float> operator*(cx<float> a, cx<float> b) {
-  const float2 t = __fmul2_rn(make_float2(a.r, a.r), f2_(b));
-  return cf_(__ffma2_rn(make_float2(-a.i, a.i), make_float2(b.i, b.r), t));
-}
-__device__ __forceinline__ cx<float> axpy(float k, cx<float> b, cx<float> a) {
-  return cf_(__ffma2_rn(make_float2(k, k), f2_(b), f2_(a)));
-}
-__device__ __forceinline__ cx<float> cfma(cx<float> b, cx<float> c, cx<float> a) {
-  const float2 t = __ffma2_rn(make_float2(b.r, b.r), f2_(c), f2_(a));
-  return cf_(__ffma2_rn(make_float2(-b.i, b.i), make_float2(c.i, c.r), t));
-}
-#endif
-
 // ------------------------------------------------------------------------------- constants
 constexpr int kSeriesMax = 20;         // max Taylor terms of the small-|z| branch
 constexpr int kSeriesF32 = 9;          // terms used by the FP32 kernels (|z| < 1/2)

@@ -90,6 +90,56 @@ __host__ __device__ __forceinline__ cdf cmk(df r, df i) {
   z.i = i;
   return z;
 }
+
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000) && !defined(BEM_NO_F32X2)
+// Complex float-float on the paired FP32 instructions of sm_100-family GPUs (FADD2 / FMUL2 /
+// FFMA2): the real and imaginary parts go through the same error-free steps side by side, one
+// paired instruction each, with the same roundings as the scalar forms below.  A difference
+// x - y is formed as fma(-1, y, x), which rounds once exactly as the subtraction does; the
+// intrinsics are never contracted.  BEM_NO_F32X2 builds the scalar forms instead.
+struct df2 {
+  float2 h, l;  // (re.h, im.h), (re.l, im.l)
+};
+__device__ __forceinline__ df2 pk(cdf a) { return {make_float2(a.r.h, a.i.h), make_float2(a.r.l, a.i.l)}; }
+__device__ __forceinline__ cdf upk(df2 a) { return cmk(dfm(a.h.x, a.l.x), dfm(a.h.y, a.l.y)); }
+__device__ __forceinline__ float2 p_sub(float2 x, float2 y) { return __ffma2_rn(make_float2(-1.f, -1.f), y, x); }
+__device__ __forceinline__ df2 p_add(df2 a, df2 b) {  // lazy sum, as add()
+  const float2 s = __fadd2_rn(a.h, b.h);
+  const float2 bb = p_sub(s, a.h);
+  const float2 e = __fadd2_rn(p_sub(a.h, p_sub(s, bb)), p_sub(b.h, bb));
+  return {s, __fadd2_rn(e, __fadd2_rn(a.l, b.l))};
+}
+__device__ __forceinline__ df2 p_neg(df2 a) {
+  return {make_float2(-a.h.x, -a.h.y), make_float2(-a.l.x, -a.l.y)};
+}
+// (k.h, k.l) broadcast times a pair, as mul()
+__device__ __forceinline__ df2 p_mul(float2 kh, float2 kl, df2 a) {
+  const float2 p = __fmul2_rn(kh, a.h);
+  float2 e = __ffma2_rn(kh, a.h, make_float2(-p.x, -p.y));
+  e = __ffma2_rn(kh, a.l, __ffma2_rn(kl, a.h, e));
+  return {p, e};
+}
+__device__ __forceinline__ cdf cadd(cdf a, cdf b) { return upk(p_add(pk(a), pk(b))); }
+__device__ __forceinline__ cdf csub(cdf a, cdf b) { return upk(p_add(pk(a), p_neg(pk(b)))); }
+__device__ __forceinline__ cdf cscale(df k, cdf a) {
+  return upk(p_mul(make_float2(k.h, k.h), make_float2(k.l, k.l), pk(a)));
+}
+__device__ __forceinline__ cdf cscalef(float k, cdf a) {
+  const df2 x = pk(a);
+  const float2 kk = make_float2(k, k);
+  const float2 p = __fmul2_rn(x.h, kk);
+  const float2 e = __ffma2_rn(x.l, kk, __ffma2_rn(x.h, kk, make_float2(-p.x, -p.y)));
+  return upk({p, e});
+}
+// (a.r b.r - a.i b.i, a.r b.i + a.i b.r) = a.r (b.r, b.i) + a.i (-b.i, b.r)
+__device__ __forceinline__ cdf cmul(cdf a, cdf b) {
+  const df2 x = pk(b);
+  const df2 y = {make_float2(-b.i.h, b.r.h), make_float2(-b.i.l, b.r.l)};
+  const df2 u = p_mul(make_float2(a.r.h, a.r.h), make_float2(a.r.l, a.r.l), x);
+  const df2 v = p_mul(make_float2(a.i.h, a.i.h), make_float2(a.i.l, a.i.l), y);
+  return upk(p_add(u, v));
+}
+#else
 __device__ __forceinline__ cdf cadd(cdf a, cdf b) { return cmk(add(a.r, b.r), add(a.i, b.i)); }
 __device__ __forceinline__ cdf csub(cdf a, cdf b) { return cmk(sub(a.r, b.r), sub(a.i, b.i)); }
 __device__ __forceinline__ cdf cmul(cdf a, cdf b) {
@@ -97,6 +147,7 @@ __device__ __forceinline__ cdf cmul(cdf a, cdf b) {
 }
 __device__ __forceinline__ cdf cscale(df k, cdf a) { return cmk(mul(k, a.r), mul(k, a.i)); }
 __device__ __forceinline__ cdf cscalef(float k, cdf a) { return cmk(mulf(a.r, k), mulf(a.i, k)); }
+#endif
 
 // ---------------------------------------------------------------------------- exp(-x), x >= 0
 struct DfConst {
