@@ -14,7 +14,10 @@ namespace bem {
 
 namespace {
 
-constexpr int kTB = 128, kS = 32, kFT = 4;
+#ifndef BEM_RESID_FT
+#define BEM_RESID_FT 4  // frequencies per CTA (a build-time choice: registers and shared memory)
+#endif
+constexpr int kTB = 128, kS = 32, kFT = BEM_RESID_FT;
 constexpr int kSeriesDf = 9;            // |z| < 0.1: 9 Taylor terms of J reach 1e-15
 constexpr float kZSeriesDf2 = 0.01f;
 
