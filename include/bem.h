@@ -79,9 +79,10 @@ typedef struct bem_options {
                           whose refinement stalls (< 4x per step) or that exhausts the cap is
                           solved again in plain FP64 from x0 = 0                             */
   double tol;          /* target ||b - A x||_2 / ||b||_2, measured in FP64 (default 1e-6)   */
-  double inner_tol;    /* relative reduction asked of each FP32 inner solve (default 2e-7;
-                          never below 0.8 tol of the right-hand side for a frequency's first
-                          inner solve, 0.5 tol for its later ones)                          */
+  double inner_tol;    /* relative reduction asked of each FP32 inner solve (default 1e-6,
+                          the FP32 operator's error floor: a first solve relative to |b|,
+                          later ones relative to the FP64-class residual; never below 0.8 tol
+                          of |b| for a frequency's first inner solve, 0.5 tol for later ones) */
   int32_t warm_start;  /* BEM_WARM_* (default ZERO)                                          */
   int32_t reserved0[2]; /* zero                                                              */
   int32_t residual_mode; /* MIXED refinement residual: BEM_RESID_DF64 (default) or

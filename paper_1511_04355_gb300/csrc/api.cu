@@ -134,7 +134,7 @@ int bem_default_options(bem_options* o) {
   o->max_iters = 500;
   o->max_refine = 8;
   o->tol = 1e-6;
-  o->inner_tol = 2e-7;
+  o->inner_tol = 1e-6;
   o->warm_start = BEM_WARM_ZERO;
   o->residual_mode = BEM_RESID_DF64;
   return BEM_OK;
