@@ -10,8 +10,8 @@ the launch configuration the benchmark uses, on outputs the oracle can compute o
   (tests/golden/cavity5120_lu.npz, written by make_cavity5120_lu.py from the oracle alone),
   elementwise: every entry against the largest LU entry.  A residual of tol ||b|| bounds the
   error by ||A^-1|| ||A|| tol, and the measured amplification reaches ~5 at the top of the band,
-  so the bounds are 1e-5 at the benchmark tolerance 1e-6, 1e-6 at tol 2e-7 (the tolerance at
-  which the mixed path's solutions meet 1e-6) and 1e-8 at tol 1e-9.
+  so the bounds are 1e-5 at the benchmark tolerance 1e-6, 1e-6 at tol 1.5e-7 (the tolerance at
+  which the mixed path's solutions meet 1e-6 at every benchmark frequency) and 1e-8 at tol 1e-9.
 """
 import os
 
@@ -99,7 +99,7 @@ def test_benchmark_solve_residuals():
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "cavity5120_lu.npz")
 
 
-@pytest.mark.parametrize("tol,bound", [(1e-6, 1e-5), (2e-7, 1e-6), (1e-9, 1e-8)])
+@pytest.mark.parametrize("tol,bound", [(1e-6, 1e-5), (1.5e-7, 1e-6), (1e-9, 1e-8)])
 def test_benchmark_solve_matches_dense_lu_elementwise(tol, bound):
     import torch
     import paper_1511_04355_gb300 as P
