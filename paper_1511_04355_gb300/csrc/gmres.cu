@@ -2,7 +2,10 @@
 // the linear solver of Sec. 2.1 ("the linear system is solved iteratively by GMRES", with the
 // block-diagonal preconditioner of Sec. 4), run for every frequency of the batch at once.
 //
-// Outer loop (FP64):   r = b - A x   (FP64 matrix-free operator)
+// Outer loop (FP64-class): r = b - A x, formed in one sweep with b recomputed from the boundary
+//                      data (float-float operator on the FP32 pipes by default, native FP64 with
+//                      residual_mode BEM_RESID_FP64); later steps of a frequency update it,
+//                      r <- r - A d, with the inner solve's correction d
 //                      stop instance f when ||r_f|| <= tol ||b_f||
 // Inner loop (precision T = float in MIXED mode, double in FP64 mode):
 //                      GMRES(m) on A M^{-1} y = r, x += M^{-1} V y
