@@ -650,15 +650,16 @@ def afs_vs_fsm(label, pb, dofs, n_orf, period, nc, J0, warm, restart=200, extra=
     c.close()
 
 
-def workload_porous_afs(full=False):
+def workload_porous_afs(full=False, lowband=False):
     """The porous-block workload: a 1 m block with 27 seeded spherical voids (radii 0.08-0.15 m),
     traction on z = 0, z = 1 fixed; the step response of six unknowns by a 256-frequency FSM and
     by AFS over the same band.  full: the ~30000-triangle recipe (42 x 42 grid per face, level-2
     voids), 256 frequencies over a 40 ms period (Omega ~ 40000 rad/s); else a reduced mesh (20 x
     20 per face, level-1 voids, 6960 triangles), 128 frequencies over a 50 ms period (Omega =
-    127 x 2 pi / 0.05 ~ 16000 rad/s, ~5.5 elements per shear wavelength).  GMRES(200): box
-    problems with a fixed face need hundreds of iterations at the upper frequencies, where
-    GMRES(50) restarts stall."""
+    127 x 2 pi / 0.05 ~ 16000 rad/s, ~5.5 elements per shear wavelength); lowband: the reduced
+    mesh, 64 frequencies over a 0.1 s period (Omega ~ 4000 rad/s, a band holding a few elastic
+    modes of the block).  GMRES(200): box problems with a fixed face need hundreds of
+    iterations at the upper frequencies, where GMRES(50) restarts stall."""
     if full:
         pb = W.porous_block(n=(42, 42, 42), n_voids=27, void_level=2)
     else:
@@ -677,18 +678,21 @@ def workload_porous_afs(full=False):
                      3 * nearest(face == 4, [0.25, 0.75, 0.0]) + 2,
                      3 * int(voids[-1]) + 2])
     period, nc = (2 * T_WIN, 256) if full else (0.05, 128)
+    if lowband:   # the same mesh over a band holding few modes: 64 frequencies over a 0.1 s period
+        period, nc = 0.1, 64
     label = (f"porous block 1x1x1 m, 27 voids, {len(f)} triangles ({3 * len(f)} unknowns), step traction "
              "on z=0, z=1 fixed")
     afs_vs_fsm(label, pb, dofs, 4, period, nc, 8, 1, max_samples=nc + nc // 2)
 
 
-def workload_example3(warm=0, n=(12, 12, 18), void_level=1):
+def workload_example3(warm=0, n=(12, 12, 18), void_level=1, nc=240):
     """The paper's third example (Sec. 4, Example 3): the 1 x 1 x 1.5 m aluminium block with 98
     cavities of radius 0.072 m, fixed on z = 1.5, step traction on z = 0; period T = 0.035 s, FSM
     with N_s = 478 (N_c = 240) against AFS with the paper's parameters (J0 = 16, alpha 2.0 / 2.3,
     E1 < 1e-4, E2 < 2e-3, J_c = 3) and six observation responses (two tractions on the fixed
     face, four displacements), two test unknowns (u_z on the loaded face, t_z on the fixed face).
-    The paper reports N_c = 240 (FSM) against 61 (AFS) for its 18080 quadratic elements."""
+    The paper reports N_c = 240 (FSM) against 61 (AFS) for its 18080 quadratic elements.  nc: FSM
+    frequencies N_s / 2 + 1 over the same period (57: a band of ~10000 rad/s, a few modes)."""
     pb = W.example3_block(n=n, void_level=void_level)
     v, f = pb["verts"], pb["tris"]
     face = pb["face"]
@@ -708,8 +712,8 @@ def workload_example3(warm=0, n=(12, 12, 18), void_level=1):
                      3 * nearest(face == 5, [0.6, 0.8, 1.5]) + 2])       # test: t_z, fixed face
     label = (f"block 1x1x1.5 m with 98 cavities r=0.072 m (Example 3), aluminium, {len(f)} triangles "
              f"({3 * len(f)} unknowns), fixed z=1.5, step traction on z=0")
-    afs_vs_fsm(label, pb, dofs, 6, 0.035, 240, 16, warm, extra={"paper_nc": {"fsm": 240, "afs": 61}},
-               max_samples=320)
+    afs_vs_fsm(label, pb, dofs, 6, 0.035, nc, 16, warm, extra={"paper_nc": {"fsm": 240, "afs": 61}},
+               max_samples=nc + nc // 3)
 
 
 def workload_large(n_freq=8):
@@ -774,7 +778,8 @@ def main():
     ap.add_argument("--profile-step", action="store_true",
                     help="run one benchmark solve with kernel counts (for ncu instruction counters)")
     ap.add_argument("--workload", choices=["uneven", "porous-afs", "porous-afs-full", "example3",
-                                           "example3-mlp", "large"],
+                                           "example3-mlp", "large", "porous-afs-lowband",
+                                           "example3-lowband"],
                     help="run one of the other workloads instead of the benchmark (own JSON line)")
     args = ap.parse_args()
     if args.kernel_case:
@@ -786,8 +791,11 @@ def main():
     if args.workload == "uneven":
         workload_uneven()
         return
-    if args.workload in ("porous-afs", "porous-afs-full"):
-        workload_porous_afs(full=args.workload == "porous-afs-full")
+    if args.workload in ("porous-afs", "porous-afs-full", "porous-afs-lowband"):
+        workload_porous_afs(full=args.workload == "porous-afs-full", lowband=args.workload == "porous-afs-lowband")
+        return
+    if args.workload == "example3-lowband":
+        workload_example3(warm=1, nc=57)   # N_s = 112 over T = 0.035 s: Omega ~ 10000 rad/s
         return
     if args.workload == "large":
         workload_large()
