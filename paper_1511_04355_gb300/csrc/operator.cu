@@ -752,19 +752,20 @@ int64_t stage_flist(bem_ctx* ctx, const std::vector<int32_t>* flist, int rec_ft)
   return n;
 }
 
-// Resident CTAs per SM of an FP32 far-kernel instantiation (occupancy query, cached).
+// Resident CTAs per SM of an FP32 far-kernel instantiation (occupancy query, made once; the
+// initialisation of a function-local static is thread-safe, and contexts on host threads of
+// bem_solve_batch may launch concurrently).
 template <int FT, bool REC>
 static int far32_per_sm() {
-  static int n = 0;
-  if (!n) {
+  static const int n = [] {
     constexpr int TB = Cfg<float>::TB, S = Cfg<float>::S;
     const size_t smem = far_smem<float, TB, S, FT, false>();
     BEM_CUDA(cudaFuncSetAttribute(far32_kernel<TB, S, FT, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
     int b = 0;
     BEM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, far32_kernel<TB, S, FT, REC>, TB, smem));
-    n = std::max(b, 1);
-  }
+    return std::max(b, 1);
+  }();
   return n;
 }
 
