@@ -767,6 +767,7 @@ def workload_large(n_freq=8):
 
 
 def main():
+    global AFS_TOL
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
@@ -775,6 +776,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the small operator/residual case used for ncu captures")
+    ap.add_argument("--afs-tol", type=float, default=AFS_TOL,
+                    help="residual tolerance of the AFS samples in the AFS-vs-FSM workloads")
     ap.add_argument("--profile-step", action="store_true",
                     help="run one benchmark solve with kernel counts (for ncu instruction counters)")
     ap.add_argument("--workload", choices=["uneven", "porous-afs", "porous-afs-full", "example3",
@@ -782,6 +785,7 @@ def main():
                                            "example3-lowband"],
                     help="run one of the other workloads instead of the benchmark (own JSON line)")
     args = ap.parse_args()
+    AFS_TOL = args.afs_tol
     if args.kernel_case:
         kernel_case()
         return

@@ -33,3 +33,14 @@ def test_reference_arm_other_ranks_print_nothing(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
     bench.run_reference(argparse.Namespace(warmup=3, steps=2, gpus=2))
     assert capsys.readouterr().out == ""
+
+
+def test_command_line_parses():
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    p = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--help"], capture_output=True, text=True)
+    assert p.returncode == 0, p.stderr
+    for opt in ("--gpus", "--steps", "--warmup", "--impl", "--workload", "--afs-tol"):
+        assert opt in p.stdout
