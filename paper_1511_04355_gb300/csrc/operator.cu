@@ -537,11 +537,17 @@ __device__ __forceinline__ void add_point(R xi0, R xi1, R xi2, const typename V4
   if (useU) u_contract(K, p.w * wsign * rinv * m.inv4pimu, rh0, rh1, rh2, vU[0], vU[1], vU[2], o);
 }
 
-template <class R>
+// WARP = false: one thread per (listed frequency, target), the near sources in sequence (many
+// frequencies fill the GPU).  WARP = true: one warp per (listed frequency, target), its lanes
+// over the (near source, point) pairs and a shuffle reduction, for launches with few frequencies
+// (a single AFS frequency on 6960 triangles launched only 55 blocks of threads and took 0.38 ms).
+template <class R, bool WARP>
 __global__ void near_kernel(const NearArgs<R> a) {
   using V = typename V4<R>::T;
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= a.nfl * a.ne) return;
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t t = WARP ? gt >> 5 : gt;
+  const int lane = WARP ? (int)(threadIdx.x & 31) : 0;
+  if (t >= a.nfl * a.ne) return;  // WARP: the same t for every lane of a warp
   const int64_t f = a.flist[t / a.ne], i = t % a.ne;
   const V c = a.cen[i];
   const FreqC<R> fc = a.fc[f];
@@ -571,17 +577,40 @@ __global__ void near_kernel(const NearArgs<R> a) {
     }
     nvT = mk(nn.x * vT[0].r + nn.y * vT[1].r + nn.z * vT[2].r, nn.x * vT[0].i + nn.y * vT[1].i + nn.z * vT[2].i);
   };
-  for (int32_t p = a.ptr[i]; p < a.ptr[i + 1]; ++p) {
-    const int64_t e = a.col[p];
-    cx<R> vT[3], vU[3], nvT;
-    bool useT, useU;
-    R sign;
-    load(e, vT, nvT, vU, useT, useU, sign);
-    const V nn = a.nrm[e];
-    for (int q = 0; q < 7; ++q)
-      add_point(c.x, c.y, c.z, a.q7[7 * e + q], sign, nn, useT, useU, fc, a.m, vT, nvT, vU, o);
-    for (int q = 0; q < 4; ++q)
-      add_point(c.x, c.y, c.z, a.q4[4 * e + q], -sign, nn, useT, useU, fc, a.m, vT, nvT, vU, o);
+  if constexpr (WARP) {
+    const int32_t p0 = a.ptr[i];
+    const int32_t nwork = (a.ptr[i + 1] - p0) * 11;
+    for (int32_t w = lane; w < nwork; w += 32) {
+      const int64_t e = a.col[p0 + w / 11];
+      const int q = w % 11;
+      cx<R> vT[3], vU[3], nvT;
+      bool useT, useU;
+      R sign;
+      load(e, vT, nvT, vU, useT, useU, sign);
+      const V nn = a.nrm[e];
+      if (q < 7) add_point(c.x, c.y, c.z, a.q7[7 * e + q], sign, nn, useT, useU, fc, a.m, vT, nvT, vU, o);
+      else add_point(c.x, c.y, c.z, a.q4[4 * e + (q - 7)], -sign, nn, useT, useU, fc, a.m, vT, nvT, vU, o);
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      for (int off = 16; off > 0; off >>= 1) {
+        o[r].r += __shfl_down_sync(0xffffffffu, o[r].r, off);
+        o[r].i += __shfl_down_sync(0xffffffffu, o[r].i, off);
+      }
+    if (lane != 0) return;
+  } else {
+    for (int32_t p = a.ptr[i]; p < a.ptr[i + 1]; ++p) {
+      const int64_t e = a.col[p];
+      cx<R> vT[3], vU[3], nvT;
+      bool useT, useU;
+      R sign;
+      load(e, vT, nvT, vU, useT, useU, sign);
+      const V nn = a.nrm[e];
+      for (int q = 0; q < 7; ++q)
+        add_point(c.x, c.y, c.z, a.q7[7 * e + q], sign, nn, useT, useU, fc, a.m, vT, nvT, vU, o);
+      for (int q = 0; q < 4; ++q)
+        add_point(c.x, c.y, c.z, a.q4[4 * e + q], -sign, nn, useT, useU, fc, a.m, vT, nvT, vU, o);
+    }
   }
   // own element from the FP64 singular blocks: H_ii' = 1/2 I + H_ii applied to vT, G_ii to vU
   {
@@ -886,7 +915,12 @@ static void launch_near(bem_ctx* ctx, const cx<R>* x, cx<R>* y, int which, int64
   a.F = ctx->fs.F;
   a.m = Geo<R>::m(ctx);
   ProfScope ps(ctx, sizeof(R) == 4 ? PK_NEAR32 : PK_NEAR64, nfl);
-  near_kernel<R><<<grid_for(nfl * a.ne, 128), 128, 0, ctx->stream>>>(a);
+  // a warp per target when one thread per target would leave the SMs mostly idle
+  const int64_t items = nfl * a.ne;
+  if (items < (int64_t)4 * 128 * (ctx->n_sm > 0 ? ctx->n_sm : 152))
+    near_kernel<R, true><<<grid_for(32 * items, 128), 128, 0, ctx->stream>>>(a);
+  else
+    near_kernel<R, false><<<grid_for(items, 128), 128, 0, ctx->stream>>>(a);
   BEM_LAUNCHED();
   ctx->launches++;
 }
