@@ -483,6 +483,29 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def kernel_case_single():
+    """Small case for ncu captures of a single-frequency FP32 operator launch (the AFS step's
+    shape): the 5120-triangle cavity at s_64 alone, one FP32 application after a warm-up."""
+    import torch
+
+    import paper_1511_04355_gb300 as P
+
+    prob = W.spherical_cavity(level=LEVEL, n_freq=N_FREQ, T=T_WIN, sigma=SIGMA)
+    c = P.Context(0)
+    c.set_mesh(prob.verts, prob.tris)
+    m = prob.material
+    c.set_material(m.mu, m.nu, m.rho)
+    c.set_bc(prob.bc_type, prob.bc_value)
+    ne = len(prob.tris)
+    s = prob.s[64:65]
+    x = torch.from_numpy(W.random_complex_vectors(1, 3 * ne) * 1e-6).cuda()
+    y = torch.zeros_like(x)
+    for _ in range(2):
+        P.bem_apply(c.h, s, x, y, P.BEM_PREC_FP32, P.BEM_APPLY_A)
+    torch.cuda.synchronize()
+    print("single-frequency kernel case done: units", ne * (ne - 1) * 4)
+
+
 def kernel_case():
     """Small case for ncu captures of the operator kernels: the 5120-triangle cavity, 24
     consecutive benchmark frequencies (s_52 .. s_75, equally spaced: the FP32 operator runs them
@@ -778,6 +801,8 @@ def main():
                     help="run only the small operator/residual case used for ncu captures")
     ap.add_argument("--afs-tol", type=float, default=AFS_TOL,
                     help="residual tolerance of the AFS samples in the AFS-vs-FSM workloads")
+    ap.add_argument("--kernel-case-single", action="store_true",
+                    help="run only the single-frequency FP32 operator case used for ncu captures")
     ap.add_argument("--profile-step", action="store_true",
                     help="run one benchmark solve with kernel counts (for ncu instruction counters)")
     ap.add_argument("--workload", choices=["uneven", "porous-afs", "porous-afs-full", "example3",
@@ -788,6 +813,9 @@ def main():
     AFS_TOL = args.afs_tol
     if args.kernel_case:
         kernel_case()
+        return
+    if args.kernel_case_single:
+        kernel_case_single()
         return
     if args.profile_step:
         profile_step()
