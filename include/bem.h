@@ -68,6 +68,10 @@ extern "C" {
 #define BEM_WARM_NEAREST 1  /* x0 = alpha * the stored solution at the nearest frequency     */
 #define BEM_WARM_MLP 2      /* x0 = a1 POD basis MLP(s) + a2 nearest stored solution, (a1, a2)
                                minimising |b - A x0| (network trained by bem_warm_train)       */
+#define BEM_WARM_VF 3       /* inside bem_afs: x0 = a1 x_VF(s) + a2 nearest stored solution, x_VF
+                               the rational prediction of every unknown from the current fit's
+                               poles (residues identified over the stored solutions, Sec. 2.3);
+                               elsewhere the nearest stored solution                           */
 
 typedef struct bem_ctx bem_ctx;
 
@@ -336,7 +340,7 @@ typedef struct bem_afs_stats {
   double seconds_solve, seconds_fit; /* out: time in BEM solves / in fitting             */
   double seconds_train;     /* out: time spent training the warm-start network            */
   int32_t warm_trainings;   /* out: trainings of the warm-start network                   */
-  int32_t warm_learned_gains; /* out: learned-start solves whose combined start left an initial
+  int32_t warm_learned_gains; /* out: MLP- or VF-start solves whose combined start left an initial
                                residual at least 10 % below the nearest stored solution's alone */
 } bem_afs_stats;
 
@@ -349,12 +353,16 @@ int bem_default_afs_params(bem_afs_params* p);
  * BEM system (one batched GPU solve, the context's options) at the frequency where the fits
  * disagree most, and stops when the time-domain change E1 and the fit discrepancy E2 of the
  * test unknowns test[Kt] stay below their thresholds for Jc + 1 consecutive steps.
- * Warm start: when the context's warm_start option is BEM_WARM_NEAREST or BEM_WARM_MLP, the call
+ * Warm start: when the context's warm_start option is BEM_WARM_NEAREST, BEM_WARM_MLP or BEM_WARM_VF, the call
  * first clears the warm-start memory, then stores every solution it computes (up to 256) and so
  * starts each new frequency's GMRES from the solutions already sampled; with BEM_WARM_MLP it
  * trains the network (default bem_warm_params) after the initial frequencies and again every
  * params->warm_retrain new samples; each learned start is combined with the nearest stored
- * solution (see BEM_WARM_MLP).  The GMRES tolerance is unchanged. 
+ * solution (see BEM_WARM_MLP); with BEM_WARM_VF each new frequency's start combines the nearest
+ * stored solution with the prediction of the step's order-M_H fit: the residues of every
+ * unknown for the fit's poles, identified by least squares over the stored solutions (the
+ * paper's residue identification of Sec. 2.3), evaluated at the new frequency.  The GMRES
+ * tolerance is unchanged. 
  * resp_out[nt_out x (K + Kt)] (host or device): time responses of the ORFs then the test
  * unknowns at t_out[nt_out] (Eq. (vf-td), final fit); stats nullable.
  * Errors: INVALID_ARG, NOT_CONVERGED (a frequency solve failed), NO_MESH, CUDA. */

@@ -89,6 +89,64 @@ StepOut afs_step(const std::vector<cd>& s, const std::vector<cd>& F, int nobs, i
   return o;
 }
 
+// Rational-prediction weights (BEM_WARM_VF).  With the fit's poles a_m, the residues of every
+// unknown follow by least squares over the stored solutions x_j = x(s_j) (the paper's residue
+// identification, Sec. 2.3): min |Phi R - X| with Phi[j][m] = 1/(s_j - a_m).  The prediction at
+// s*, phi*^T R = phi*^T Phi^+ X, is a combination of the stored solutions with weights
+// w = conj(Q) u, where Phi D^{-1} = Q R' (modified Gram-Schmidt on the unit-scaled columns D) and
+// R'^T u = D^{-1} phi*.  Columns whose pivot falls below 1e-12 of the largest are dropped.
+// Returns false (no weights) when fewer solutions than poles are stored.
+bool vf_weights(const std::vector<cd>& poles, const std::vector<double>& s_stored, int64_t J,
+                const std::vector<cd>& targets, std::vector<cx<double>>& w) {
+  const int M = (int)poles.size();
+  if (M < 1 || J < M + 1) return false;
+  std::vector<cd> Q((size_t)J * M), R((size_t)M * M, cd(0, 0));
+  std::vector<double> d(M);
+  for (int m = 0; m < M; ++m) {
+    double nrm = 0;
+    for (int64_t j = 0; j < J; ++j) {
+      const cd v = 1.0 / (cd(s_stored[2 * j], s_stored[2 * j + 1]) - poles[m]);
+      Q[(size_t)j * M + m] = v;
+      nrm += std::norm(v);
+    }
+    d[m] = nrm > 0 ? std::sqrt(nrm) : 1.0;
+    for (int64_t j = 0; j < J; ++j) Q[(size_t)j * M + m] /= d[m];
+  }
+  for (int m = 0; m < M; ++m) {  // modified Gram-Schmidt
+    for (int k = 0; k < m; ++k) {
+      cd dot(0, 0);
+      for (int64_t j = 0; j < J; ++j) dot += std::conj(Q[(size_t)j * M + k]) * Q[(size_t)j * M + m];
+      R[(size_t)k * M + m] = dot;
+      for (int64_t j = 0; j < J; ++j) Q[(size_t)j * M + m] -= dot * Q[(size_t)j * M + k];
+    }
+    double nrm = 0;
+    for (int64_t j = 0; j < J; ++j) nrm += std::norm(Q[(size_t)j * M + m]);
+    nrm = std::sqrt(nrm);
+    R[(size_t)m * M + m] = nrm;
+    if (nrm > 0)
+      for (int64_t j = 0; j < J; ++j) Q[(size_t)j * M + m] /= nrm;
+  }
+  double rmax = 0;
+  for (int m = 0; m < M; ++m) rmax = std::max(rmax, std::abs(R[(size_t)m * M + m]));
+  w.assign(targets.size() * (size_t)J, mk(0.0, 0.0));
+  for (size_t f = 0; f < targets.size(); ++f) {
+    std::vector<cd> u(M, cd(0, 0));
+    for (int m = 0; m < M; ++m) {
+      const double rmm = std::abs(R[(size_t)m * M + m]);
+      if (rmm <= 1e-12 * rmax) continue;  // dependent column: dropped
+      cd acc = 1.0 / (targets[f] - poles[m]) / d[m];
+      for (int k = 0; k < m; ++k) acc -= R[(size_t)k * M + m] * u[k];
+      u[m] = acc / R[(size_t)m * M + m];
+    }
+    for (int64_t j = 0; j < J; ++j) {
+      cd acc(0, 0);
+      for (int m = 0; m < M; ++m) acc += u[m] * std::conj(Q[(size_t)j * M + m]);
+      w[f * J + j] = mk(acc.real(), acc.imag());
+    }
+  }
+  return true;
+}
+
 }  // namespace
 
 }  // namespace bem
@@ -335,6 +393,21 @@ int bem_afs(bem_ctx* ctx, const bem_afs_params* prm, const int64_t* orf, int64_t
         const double wb = grid[gbest].imag();
         for (int g = 0; g < p.n_grid; ++g)
           if (std::fabs(grid[g].imag() - wb) <= half) d[g] = -1.0;
+      }
+      if (wmode == BEM_WARM_VF) {
+        // the next solve starts from the current fit's rational prediction (and the nearest
+        // stored solution): weights over the stored solutions for each pick
+        WarmStart& ws = ctx->warm;
+        const int64_t Js = (int64_t)(ws.s.size() / 2);
+        ws.vf_J = 0;
+        ws.vf_s.clear();
+        if (vf_weights(so.H.poles, ws.s, Js, picks, ws.vf_w)) {
+          ws.vf_J = Js;
+          for (const cd& z : picks) {
+            ws.vf_s.push_back(z.real());
+            ws.vf_s.push_back(z.imag());
+          }
+        }
       }
       std::vector<cd> Fn;
       solve(picks, Fn);

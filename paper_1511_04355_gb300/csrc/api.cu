@@ -219,7 +219,7 @@ int bem_set_options(bem_ctx* ctx, const bem_options* o) {
     BEM_REQUIRE(o->max_iters >= 1, "max_iters must be >= 1");
     BEM_REQUIRE(o->tol > 0 && o->tol < 1, "tol must be in (0, 1)");
     BEM_REQUIRE(o->inner_tol > 0 && o->inner_tol < 1, "inner_tol must be in (0, 1)");
-    BEM_REQUIRE(o->warm_start >= BEM_WARM_ZERO && o->warm_start <= BEM_WARM_MLP, "bad warm_start");
+    BEM_REQUIRE(o->warm_start >= BEM_WARM_ZERO && o->warm_start <= BEM_WARM_VF, "bad warm_start");
     BEM_REQUIRE(o->residual_mode == BEM_RESID_DF64 || o->residual_mode == BEM_RESID_FP64,
                 "residual_mode must be BEM_RESID_DF64 or BEM_RESID_FP64");
     ctx->opt = *o;

@@ -243,6 +243,11 @@ struct WarmStart {
   DevBuf act;                 // activations scratch
   double omega = 1;
   bool trained = false;
+  // rational-prediction weights (BEM_WARM_VF, set by the AFS driver for its next solve):
+  // x(vf_s[f]) ~ sum_j vf_w[f][j] X[j] over the first vf_J stored solutions
+  std::vector<double> vf_s;         // 2F: frequencies the weights are for
+  std::vector<cx<double>> vf_w;     // [F][vf_J]
+  int64_t vf_J = 0;
 };
 
 }  // namespace bem

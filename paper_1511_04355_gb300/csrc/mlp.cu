@@ -213,6 +213,17 @@ __global__ void expand_kernel(const float* y, const cx<double>* Phi, int64_t N, 
   x0[t] = s;
 }
 
+// x0[f][n] = sum_j w[f][j] X[j][n]: the rational prediction from the stored solutions
+__global__ void weighted_sum_kernel(const cx<double>* w, const cx<double>* X, int64_t N, int64_t J, int64_t F,
+                                    cx<double>* x0) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= N * F) return;
+  const int64_t f = t / N, n = t % N;
+  cx<double> s = mk(0.0, 0.0);
+  for (int64_t j = 0; j < J; ++j) s = cfma(w[f * J + j], X[j * N + n], s);
+  x0[t] = s;
+}
+
 // C[j][k] = (Phi^H x_j)_k (one block per (j, k))
 __global__ void project_kernel(const cx<double>* Phi, const cx<double>* X, int64_t N, int r, cx<double>* C) {
   __shared__ double sr[256], si[256];
@@ -567,6 +578,23 @@ void warm_initial(bem_ctx* ctx, int mode, const double* s, int64_t F, cx<double>
   WarmStart& ws = ctx->warm;
   const int64_t N = 3 * ctx->mesh.ne;
   BEM_REQUIRE(ws.N == N && !ws.s.empty(), "warm start requested but no stored solutions match the mesh");
+  if (mode == BEM_WARM_VF) {
+    // weights for exactly these frequencies, else the nearest stored solution
+    bool have = ws.vf_J > 0 && (int64_t)ws.vf_s.size() == 2 * F && ws.vf_J <= (int64_t)(ws.s.size() / 2);
+    for (int64_t k = 0; have && k < 2 * F; ++k) have = ws.vf_s[k] == s[k];
+    if (have) {
+      DevBuf dw;
+      dw.reserve(sizeof(cx<double>) * F * ws.vf_J);
+      copy_in(ctx, dw.p, ws.vf_w.data(), sizeof(cx<double>) * F * ws.vf_J);
+      weighted_sum_kernel<<<grid_for(N * F, 256), 256, 0, ctx->stream>>>(dw.as<cx<double>>(), ws.X.as<cx<double>>(),
+                                                                          N, ws.vf_J, F, x0);
+      BEM_LAUNCHED();
+      ctx->launches++;
+      BEM_CUDA(cudaStreamSynchronize(ctx->stream));  // dw is released on return
+      return;
+    }
+    mode = BEM_WARM_NEAREST;
+  }
   if (mode == BEM_WARM_NEAREST) {
     const int J = (int)(ws.s.size() / 2);
     for (int64_t f = 0; f < F; ++f) {

@@ -1,10 +1,11 @@
 """The warm start inside AFS (Sec. 3, Algorithm AFS: each adaptive step solves one new frequency
 next to the frequencies already solved), through bem_afs.
 
-For each workload bem_afs runs three times, with the context's warm_start set to ZERO (GMRES
-from x0 = 0), NEAREST (the stored solution at the nearest sampled frequency) and MLP (the POD +
+For each workload bem_afs runs four times, with the context's warm_start set to ZERO (GMRES
+from x0 = 0), NEAREST (the stored solution at the nearest sampled frequency), MLP (the POD +
 MLP prediction, retrained every 4 samples, combined with the nearest solution by minimal
-residual).
+residual) and VF (the rational prediction of every unknown from the step's fitted poles,
+combined with the nearest solution the same way).
 The warm start may change the GMRES iterations only: every run must sample the same number of
 frequencies (within 2, since the greedy choice can take another branch on rounding-level
 differences of the solutions) and return the same transients (within 2e-3 of the largest
@@ -71,7 +72,8 @@ def test_afs_warm_start_modes(case):
     P = _P()
     c, opts, orf, test, prm, t = _cavity() if case == "cavity320" else _rod()
     runs = {}
-    for name, mode in (("zero", P.BEM_WARM_ZERO), ("nearest", P.BEM_WARM_NEAREST), ("mlp", P.BEM_WARM_MLP)):
+    for name, mode in (("zero", P.BEM_WARM_ZERO), ("nearest", P.BEM_WARM_NEAREST), ("mlp", P.BEM_WARM_MLP),
+                       ("vf", P.BEM_WARM_VF)):
         c.set_options(warm_start=mode, **opts)
         p = P.bem_default_afs_params(**prm)
         out, info = c.afs(p, orf, test, t)
@@ -88,7 +90,7 @@ def test_afs_warm_start_modes(case):
         assert info["n_samples"] < prm["max_samples"]
     out0, info0 = runs["zero"]
     scale = np.abs(out0).max(axis=0)
-    for name in ("nearest", "mlp"):
+    for name in ("nearest", "mlp", "vf"):
         out, info = runs[name]
         assert abs(info["n_samples"] - info0["n_samples"]) <= 2, (name, info["n_samples"], info0["n_samples"])
         err = (np.abs(out - out0).max(axis=0) / scale).max()
@@ -98,5 +100,5 @@ def test_afs_warm_start_modes(case):
     J0 = prm["J0"]
     per = {k: runs[k][1]["gmres_iters"][J0:].mean() for k in runs}
     print(f"{case} mean adaptive-stage iterations per solve: {per}")
-    assert per["nearest"] <= per["zero"] and per["mlp"] <= per["zero"], per
+    assert per["nearest"] <= per["zero"] and per["mlp"] <= per["zero"] and per["vf"] <= per["zero"], per
     assert runs["mlp"][1]["warm_trainings"] >= 2
