@@ -72,7 +72,7 @@ FLOPS_EXEC_PER_UNIT_FAR64 = 287.4   # 7.231e11 flop over the 2.516e9 units of on
 # kernel case (5120 triangles, 24 x 5120 x 5119 x 4 units): the source vectors, the geometry and
 # the FP64 accumulator lines the atomic adds pull in, all proportional to the frequencies (units)
 # of a launch, so the roofline scales it to the benchmark's average launch
-FAR32_CAPTURE_BYTES, FAR32_CAPTURE_UNITS = 9.80864e6, 24 * 5120 * 5119 * 4
+FAR32_CAPTURE_BYTES, FAR32_CAPTURE_UNITS = 1.00224e7, 24 * 5120 * 5119 * 4
 
 
 def workload_config(n_gpus):
