@@ -607,6 +607,7 @@ def workload_uneven():
 
 
 AFS_TOL = TOL    # residual tolerance of the AFS samples (--afs-tol; see afs_vs_fsm)
+AFS_WARM = None  # warm start of the AFS samples (--afs-warm; None: the workload's own choice)
 
 
 def afs_vs_fsm(label, pb, dofs, n_orf, period, nc, J0, warm, restart=200, extra=None, max_samples=None):
@@ -643,6 +644,8 @@ def afs_vs_fsm(label, pb, dofs, n_orf, period, nc, J0, warm, restart=200, extra=
     del x
     print(json.dumps({"label": label, "fsm_seconds": t_fsm, "triangles": len(f),
                       "fsm_iterations": int(finfo["iterations"].sum())}), file=sys.stderr, flush=True)
+    if AFS_WARM is not None:
+        warm = AFS_WARM
     c.set_options(precision=P.BEM_PREC_MIXED, tol=AFS_TOL, restart=restart, max_iters=6000, max_refine=20,
                   warm_start=warm)
     prm = P.bem_default_afs_params(eta=eta, omega_max=omega, T=period, J0=J0, max_samples=max_samples or nc)
@@ -663,7 +666,7 @@ def afs_vs_fsm(label, pb, dofs, n_orf, period, nc, J0, warm, restart=200, extra=
                     "seconds_solve": info["seconds_solve"], "seconds_fit": info["seconds_fit"],
                     "seconds_train": info["seconds_train"],
                     "gmres_iterations": int(np.sum(info["gmres_iters"])),
-                    "warm_start": {0: "zero", 1: "nearest", 2: "mlp"}[warm]},
+                    "warm_start": {0: "zero", 1: "nearest", 2: "mlp", 3: "vf"}[warm]},
             "afs_vs_fsm_rel_l2": {"hanning": rel(afs_out, fsm_w), "no_window": rel(afs_out, fsm_n)},
             "fsm_hanning_vs_no_window_rel_l2": rel(fsm_w, fsm_n),
             "nc_ratio_fsm_over_afs": nc / max(int(info["n_samples"]), 1)}
@@ -790,7 +793,7 @@ def workload_large(n_freq=8):
 
 
 def main():
-    global AFS_TOL
+    global AFS_TOL, AFS_WARM
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
@@ -799,6 +802,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the small operator/residual case used for ncu captures")
+    ap.add_argument("--afs-warm", choices=["zero", "nearest", "mlp", "vf"], default=None,
+                    help="warm start of the AFS solves in the AFS-vs-FSM workloads (default nearest)")
     ap.add_argument("--afs-tol", type=float, default=AFS_TOL,
                     help="residual tolerance of the AFS samples in the AFS-vs-FSM workloads")
     ap.add_argument("--kernel-case-single", action="store_true",
@@ -811,6 +816,8 @@ def main():
                     help="run one of the other workloads instead of the benchmark (own JSON line)")
     args = ap.parse_args()
     AFS_TOL = args.afs_tol
+    if args.afs_warm:
+        AFS_WARM = {"zero": 0, "nearest": 1, "mlp": 2, "vf": 3}[args.afs_warm]
     if args.kernel_case:
         kernel_case()
         return
