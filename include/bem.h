@@ -72,6 +72,12 @@ extern "C" {
                                the rational prediction of every unknown from the current fit's
                                poles (residues identified over the stored solutions, Sec. 2.3);
                                elsewhere the nearest stored solution                           */
+#define BEM_WARM_SWEEP 4    /* a frequency list of >= 8 is solved in two passes: every other
+                               frequency from x0 = 0, then a vector fit of order J/2 to 8
+                               unknowns of those J solutions, then the remaining frequencies
+                               from the fit's rational prediction of every unknown combined with
+                               the nearest solved frequency, as BEM_WARM_VF (uses and replaces
+                               the context's warm-start memory); in bem_afs as BEM_WARM_VF     */
 
 typedef struct bem_ctx bem_ctx;
 

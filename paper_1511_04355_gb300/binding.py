@@ -39,6 +39,7 @@ BEM_WARM_ZERO = 0
 BEM_WARM_NEAREST = 1
 BEM_WARM_MLP = 2
 BEM_WARM_VF = 3
+BEM_WARM_SWEEP = 4
 BEM_KERNEL_FAR32 = 0
 BEM_KERNEL_FAR64 = 1
 BEM_KERNEL_NEAR32 = 2

@@ -89,6 +89,8 @@ StepOut afs_step(const std::vector<cd>& s, const std::vector<cd>& F, int nobs, i
   return o;
 }
 
+}  // namespace
+
 // Rational-prediction weights (BEM_WARM_VF).  With the fit's poles a_m, the residues of every
 // unknown follow by least squares over the stored solutions x_j = x(s_j) (the paper's residue
 // identification, Sec. 2.3): min |Phi R - X| with Phi[j][m] = 1/(s_j - a_m).  The prediction at
@@ -147,7 +149,118 @@ bool vf_weights(const std::vector<cd>& poles, const std::vector<double>& s_store
   return true;
 }
 
-}  // namespace
+
+// The frequency sweep of BEM_WARM_SWEEP: every other frequency first (zero start), a vector fit
+// of order J/2 (Eq. (fit-ords) with alpha 2) to K = 8 unknowns spread over the mesh at those J
+// frequencies, then the remaining frequencies from the fit's rational prediction combined with
+// the nearest solved frequency (BEM_WARM_VF).  The tolerance and the certification of every
+// frequency are unchanged.  Fewer than 8 frequencies, or a failed fit: one batch, zero start.
+void solve_frequency_list(bem_ctx* ctx, const double* sh, int64_t ns, cx<double>* x_dev,
+                          std::vector<int32_t>& it, std::vector<int32_t>& rf, std::vector<double>& res,
+                          std::vector<int32_t>& status) {
+  const bool mixed = ctx->opt.precision == BEM_PREC_MIXED;
+  const int wmode = ctx->opt.warm_start;
+  if (wmode != BEM_WARM_SWEEP || ns < 8) {
+    const int saved = ctx->opt.warm_start;
+    if (wmode == BEM_WARM_SWEEP) ctx->opt.warm_start = BEM_WARM_ZERO;
+    prepare_frequencies(ctx, sh, ns, mixed);
+    try {
+      solve_batch(ctx, x_dev, nullptr, it, rf, res, status);
+    } catch (...) {
+      ctx->opt.warm_start = saved;
+      throw;
+    }
+    ctx->opt.warm_start = saved;
+    return;
+  }
+  const int64_t N = 3 * ctx->mesh.ne;
+  std::vector<int64_t> idx[2];
+  for (int64_t f = 0; f < ns; ++f) idx[f % 2].push_back(f);
+  it.assign(ns, 0);
+  rf.assign(ns, 0);
+  res.assign(ns, 0.0);
+  status.assign(ns, 0);
+  DevBuf part;
+  WarmStart& ws = ctx->warm;
+  const int saved = ctx->opt.warm_start;
+  try {
+    for (int pass = 0; pass < 2; ++pass) {
+      const std::vector<int64_t>& I = idx[pass];
+      const int64_t F = (int64_t)I.size();
+      std::vector<double> sp(2 * F);
+      for (int64_t k = 0; k < F; ++k) {
+        sp[2 * k] = sh[2 * I[k]];
+        sp[2 * k + 1] = sh[2 * I[k] + 1];
+      }
+      part.reserve(sizeof(cx<double>) * F * N);
+      ctx->opt.warm_start = pass == 0 ? BEM_WARM_ZERO : BEM_WARM_VF;
+      prepare_frequencies(ctx, sp.data(), F, mixed);
+      std::vector<int32_t> it_p, rf_p, st_p;
+      std::vector<double> res_p;
+      solve_batch(ctx, part.as<cx<double>>(), nullptr, it_p, rf_p, res_p, st_p);
+      for (int64_t k = 0; k < F; ++k) {
+        it[I[k]] = it_p[k];
+        rf[I[k]] = rf_p[k];
+        res[I[k]] = res_p[k];
+        status[I[k]] = st_p[k];
+        BEM_CUDA(cudaMemcpyAsync(x_dev + I[k] * N, part.as<cx<double>>() + k * N, sizeof(cx<double>) * N,
+                                 cudaMemcpyDeviceToDevice, ctx->stream));
+      }
+      if (pass == 1) break;
+      // the fit of the first pass and the prediction weights of the second
+      ws.s.clear();
+      ws.trained = false;
+      ws.r = 0;
+      ws.vf_J = 0;
+      ws.vf_s.clear();
+      warm_store(ctx, sp.data(), F, part.as<cx<double>>());
+      constexpr int K = 8;
+      std::vector<int64_t> dofs(K);
+      for (int k = 0; k < K; ++k) dofs[k] = 3 * ((2 * k + 1) * ctx->mesh.ne / (2 * K)) + (k % 3);
+      DevBuf ddofs, obs;
+      ddofs.reserve(sizeof(int64_t) * K);
+      obs.reserve(sizeof(cx<double>) * F * K);
+      copy_in(ctx, ddofs.p, dofs.data(), sizeof(int64_t) * K);
+      gather_dofs(ctx, part.as<cx<double>>(), N, F, ddofs.as<int64_t>(), K, obs.as<cx<double>>());
+      std::vector<cx<double>> hv((size_t)F * K);
+      copy_out(ctx, hv.data(), obs.p, sizeof(cx<double>) * F * K);
+      std::vector<cd> sv(F), Fo((size_t)F * K);
+      double wmax = 0;
+      for (int64_t k = 0; k < F; ++k) {
+        sv[k] = cd(sp[2 * k], sp[2 * k + 1]);
+        wmax = std::max(wmax, std::fabs(sp[2 * k + 1]));
+      }
+      for (int c = 0; c < K; ++c) {
+        double mx = 0;
+        for (int64_t k = 0; k < F; ++k) mx = std::max(mx, std::hypot(hv[k * K + c].r, hv[k * K + c].i));
+        if (mx == 0) mx = 1;
+        for (int64_t k = 0; k < F; ++k) Fo[(size_t)k * K + c] = cd(hv[k * K + c].r, hv[k * K + c].i) / mx;
+      }
+      std::vector<int> cols(K);
+      for (int c = 0; c < K; ++c) cols[c] = c;
+      std::vector<cd> targets;
+      for (int64_t f : idx[1]) targets.emplace_back(sh[2 * f], sh[2 * f + 1]);
+      try {
+        const vfit::Poles PH = vfit::fit_poles(sv, Fo, K, cols, (int)(F / 2), std::max(wmax, 1.0), 20, 1e-10);
+        const vfit::Model md = vfit::residues(sv, Fo, K, PH);
+        if (vf_weights(md.poles, ws.s, F, targets, ws.vf_w)) {
+          ws.vf_J = F;
+          for (const cd& z : targets) {
+            ws.vf_s.push_back(z.real());
+            ws.vf_s.push_back(z.imag());
+          }
+        }
+      } catch (const std::exception&) {
+        // no prediction: the second pass starts from the nearest solved frequency
+      }
+    }
+  } catch (...) {
+    ctx->opt.warm_start = saved;
+    throw;
+  }
+  ctx->opt.warm_start = saved;
+  BEM_CUDA(cudaStreamSynchronize(ctx->stream));
+}
 
 }  // namespace bem
 
@@ -276,7 +389,7 @@ int bem_afs(bem_ctx* ctx, const bem_afs_params* prm, const int64_t* orf, int64_t
     double t_solve = 0, t_fit = 0, t_train = 0;
     std::vector<int32_t> solve_iters;
     // warm start: the memory holds this run's own samples only
-    const int wmode = ctx->opt.warm_start;
+    const int wmode = ctx->opt.warm_start == BEM_WARM_SWEEP ? BEM_WARM_VF : ctx->opt.warm_start;
     const int retrain = p.warm_retrain > 0 ? p.warm_retrain : 4;
     constexpr int kWarmCap = 256;  // solutions the network can be trained on
     int warm_trainings = 0, last_train = 0;

@@ -219,7 +219,7 @@ int bem_set_options(bem_ctx* ctx, const bem_options* o) {
     BEM_REQUIRE(o->max_iters >= 1, "max_iters must be >= 1");
     BEM_REQUIRE(o->tol > 0 && o->tol < 1, "tol must be in (0, 1)");
     BEM_REQUIRE(o->inner_tol > 0 && o->inner_tol < 1, "inner_tol must be in (0, 1)");
-    BEM_REQUIRE(o->warm_start >= BEM_WARM_ZERO && o->warm_start <= BEM_WARM_VF, "bad warm_start");
+    BEM_REQUIRE(o->warm_start >= BEM_WARM_ZERO && o->warm_start <= BEM_WARM_SWEEP, "bad warm_start");
     BEM_REQUIRE(o->residual_mode == BEM_RESID_DF64 || o->residual_mode == BEM_RESID_FP64,
                 "residual_mode must be BEM_RESID_DF64 or BEM_RESID_FP64");
     ctx->opt = *o;
@@ -518,11 +518,10 @@ int bem_fsm(bem_ctx* ctx, double period, double eta, int64_t nc, const double* t
       s[2 * k + 1] = 2.0 * kPi * (double)k / period;
     }
     ctx->f32_applies = ctx->f64_applies = 0;
-    prepare_frequencies(ctx, s.data(), nc, ctx->opt.precision == BEM_PREC_MIXED);
     ctx->io_a.reserve(sizeof(cx<double>) * nc * N);
     std::vector<int32_t> it, rf, status;
     std::vector<double> res;
-    solve_batch(ctx, ctx->io_a.as<cx<double>>(), stats, it, rf, res, status);
+    solve_frequency_list(ctx, s.data(), nc, ctx->io_a.as<cx<double>>(), it, rf, res, status);
     for (int64_t f = 0; f < nc; ++f) not_conv |= (status[f] != 0);
     DevBuf ddofs;
     ddofs.reserve(sizeof(int64_t) * ndofs);
@@ -566,12 +565,11 @@ int bem_solve_frequencies(bem_ctx* ctx, const double* s, int64_t ns, double* x_o
     ctx->f32_applies = ctx->f64_applies = 0;
     std::vector<double> sh(2 * ns);
     copy_out(ctx, sh.data(), s, sizeof(double) * 2 * ns);
-    prepare_frequencies(ctx, sh.data(), ns, ctx->opt.precision == BEM_PREC_MIXED);
     const int64_t n = ns * 3 * ctx->mesh.ne;
     ctx->io_a.reserve(sizeof(cx<double>) * n);
     std::vector<int32_t> it, rf, status;
     std::vector<double> res;
-    solve_batch(ctx, ctx->io_a.as<cx<double>>(), stats, it, rf, res, status);
+    solve_frequency_list(ctx, sh.data(), ns, ctx->io_a.as<cx<double>>(), it, rf, res, status);
     if (x_out) copy_out(ctx, x_out, ctx->io_a.p, sizeof(cx<double>) * n);
     for (int64_t f = 0; f < ns; ++f) not_conv |= (status[f] != 0);
     if (stats) {

@@ -349,6 +349,12 @@ struct ProfScope {
 };
 void prof_collect(bem_ctx* ctx);  // synchronises and folds finished records into totals
 
+// afs.cu: solve a frequency list (prepared inside) with the context's options, including the
+// two-pass sweep of BEM_WARM_SWEEP; per-frequency statistics in list order
+void solve_frequency_list(bem_ctx* ctx, const double* s_host, int64_t ns, cx<double>* x_dev,
+                          std::vector<int32_t>& it, std::vector<int32_t>& rf, std::vector<double>& res,
+                          std::vector<int32_t>& status);
+
 // tune.cu: the shape of an FP32 far-field launch of nfl frequencies on the context's mesh
 FarShape far32_shape(bem_ctx* ctx, int64_t nfl);
 

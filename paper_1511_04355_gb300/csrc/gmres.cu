@@ -554,8 +554,10 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
     ctx->launches++;
     BEM_CUDA(cudaMemcpyAsync(W.r.p, W.b.p, sizeof(cx<double>) * F * N, cudaMemcpyDeviceToDevice, st));
   }
-  const bool warm = o.warm_start != BEM_WARM_ZERO && ctx->warm.N == N && !ctx->warm.s.empty() &&
-                    (o.warm_start != BEM_WARM_MLP || ctx->warm.trained);
+  // a sweep's passes arrive here as ZERO or VF; a sweep option on a direct call acts as VF
+  const int wstart = o.warm_start == BEM_WARM_SWEEP ? BEM_WARM_VF : o.warm_start;
+  const bool warm = wstart != BEM_WARM_ZERO && ctx->warm.N == N && !ctx->warm.s.empty() &&
+                    (wstart != BEM_WARM_MLP || ctx->warm.trained);
   ctx->warm_learned_gains = 0;
   if (warm) {
     // direction x^ from the warm start, y = A x^ with the operator of the inner solve's
@@ -582,14 +584,14 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
     };
     DevBuf r1;
     r1.reserve(sizeof(cx<double>) * F * N);
-    if (o.warm_start == BEM_WARM_MLP || o.warm_start == BEM_WARM_VF) {
+    if (wstart == BEM_WARM_MLP || wstart == BEM_WARM_VF) {
       // predicted direction x1 (the network's Phi c(s), or the rational prediction of the AFS
       // fit) and nearest stored solution x2, combined as x0 = a1 x1 + a2 x2 with the (a1, a2)
       // minimising |b - A x0|: never worse than either alone
       DevBuf x2, rr;
       x2.reserve(sizeof(cx<double>) * F * N);
       rr.reserve(sizeof(double) * 2 * F);
-      warm_initial(ctx, o.warm_start, ctx->fs.s.data(), F, x_dev);
+      warm_initial(ctx, wstart, ctx->fs.s.data(), F, x_dev);
       warm_initial(ctx, BEM_WARM_NEAREST, ctx->fs.s.data(), F, x2.as<cx<double>>());
       if (mixed) {
         DevBuf xf, y1, y2;
@@ -624,7 +626,7 @@ void solve_batch(bem_ctx* ctx, cx<double>* x_dev, bem_solve_stats* /*st*/,
       norm2_kernel<double><<<(unsigned)F, 256, 0, st>>>(r1.as<cx<double>>(), N, nullptr, W.rn2.as<double>());
       ctx->launches++;
     } else {
-      candidate(o.warm_start, x_dev, r1.as<cx<double>>(), W.rn2.as<double>());
+      candidate(wstart, x_dev, r1.as<cx<double>>(), W.rn2.as<double>());
     }
     BEM_CUDA(cudaMemcpyAsync(W.r.p, r1.p, sizeof(cx<double>) * F * N, cudaMemcpyDeviceToDevice, st));
     BEM_CUDA(cudaStreamSynchronize(st));

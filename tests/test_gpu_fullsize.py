@@ -11,7 +11,8 @@ the launch configuration the benchmark uses, on outputs the oracle can compute o
   elementwise: every entry against the largest LU entry.  A residual of tol ||b|| bounds the
   error by ||A^-1|| ||A|| tol, and the measured amplification reaches ~5 at the top of the band,
   so the bounds are 1e-5 at the benchmark tolerance 1e-6, 1e-6 at tol 1.5e-7 (the tolerance at
-  which the mixed path's solutions meet 1e-6 at every benchmark frequency) and 1e-8 at tol 1e-9.
+  which the mixed path's solutions meet 1e-6 at every benchmark frequency) and 1e-8 at tol 1e-9;
+  the same bounds hold for the two-pass sweep (BEM_WARM_SWEEP), whose second pass starts warm.
 """
 import os
 
@@ -99,8 +100,9 @@ def test_benchmark_solve_residuals():
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "cavity5120_lu.npz")
 
 
-@pytest.mark.parametrize("tol,bound", [(1e-6, 1e-5), (1.5e-7, 1e-6), (1e-9, 1e-8)])
-def test_benchmark_solve_matches_dense_lu_elementwise(tol, bound):
+@pytest.mark.parametrize("tol,bound,sweep", [(1e-6, 1e-5, False), (1.5e-7, 1e-6, False), (1e-9, 1e-8, False),
+                                             (1e-6, 1e-5, True), (1.5e-7, 1e-6, True)])
+def test_benchmark_solve_matches_dense_lu_elementwise(tol, bound, sweep):
     import torch
     import paper_1511_04355_gb300 as P
     gold = np.load(GOLDEN)
@@ -108,7 +110,8 @@ def test_benchmark_solve_matches_dense_lu_elementwise(tol, bound):
     assert np.allclose(gold["s"], prob.s[gold["k"]], rtol=0, atol=1e-9)
     assert (gold["lu_residual"] < 1e-13).all()
     c = _ctx()
-    c.set_options(precision=P.BEM_PREC_MIXED, tol=tol)
+    c.set_options(precision=P.BEM_PREC_MIXED, tol=tol,
+                  warm_start=P.BEM_WARM_SWEEP if sweep else P.BEM_WARM_ZERO)
     ne = len(prob.tris)
     sd = torch.from_numpy(prob.s).cuda()
     xd = torch.zeros((128, 3 * ne), dtype=torch.complex128, device="cuda")
@@ -116,5 +119,6 @@ def test_benchmark_solve_matches_dense_lu_elementwise(tol, bound):
     assert (info["status"] == 0).all() and (info["residual"] <= tol).all()
     x = xd.cpu().numpy()
     errs = [max_rel_err(x[k], xl, prob.bc_type) for k, xl in zip(gold["k"], gold["x"])]
-    print(f"tol {tol}: elementwise error against dense LU at k = {gold['k'].tolist()}: {errs}")
+    print(f"tol {tol} sweep {sweep}: elementwise error against dense LU at k = {gold['k'].tolist()}: {errs}; "
+          f"GMRES iterations {int(info['iterations'].sum())}")
     assert max(errs) <= bound, errs
