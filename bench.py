@@ -682,9 +682,9 @@ def workload_porous_afs(full=False, lowband=False):
     by AFS over the same band.  full: the ~30000-triangle recipe (42 x 42 grid per face, level-2
     voids), 256 frequencies over a 40 ms period (Omega ~ 40000 rad/s); else a reduced mesh (20 x
     20 per face, level-1 voids, 6960 triangles), 128 frequencies over a 50 ms period (Omega =
-    127 x 2 pi / 0.05 ~ 16000 rad/s, ~5.5 elements per shear wavelength); lowband: the reduced
-    mesh, 64 frequencies over a 0.1 s period (Omega ~ 4000 rad/s, a band holding a few elastic
-    modes of the block).  GMRES(200): box problems with a fixed face need hundreds of
+    127 x 2 pi / 0.05 ~ 16000 rad/s, ~5.5 elements per shear wavelength); lowband: the mesh
+    chosen by full, 64 frequencies over a 0.1 s period (Omega ~ 4000 rad/s, a band holding a few
+    elastic modes of the block).  GMRES(200): box problems with a fixed face need hundreds of
     iterations at the upper frequencies, where GMRES(50) restarts stall."""
     if full:
         pb = W.porous_block(n=(42, 42, 42), n_voids=27, void_level=2)
@@ -812,7 +812,7 @@ def main():
                     help="run one benchmark solve with kernel counts (for ncu instruction counters)")
     ap.add_argument("--workload", choices=["uneven", "porous-afs", "porous-afs-full", "example3",
                                            "example3-mlp", "large", "porous-afs-lowband",
-                                           "example3-lowband"],
+                                           "porous-afs-full-lowband", "example3-lowband"],
                     help="run one of the other workloads instead of the benchmark (own JSON line)")
     args = ap.parse_args()
     AFS_TOL = args.afs_tol
@@ -830,8 +830,9 @@ def main():
     if args.workload == "uneven":
         workload_uneven()
         return
-    if args.workload in ("porous-afs", "porous-afs-full", "porous-afs-lowband"):
-        workload_porous_afs(full=args.workload == "porous-afs-full", lowband=args.workload == "porous-afs-lowband")
+    if args.workload in ("porous-afs", "porous-afs-full", "porous-afs-lowband", "porous-afs-full-lowband"):
+        workload_porous_afs(full=args.workload in ("porous-afs-full", "porous-afs-full-lowband"),
+                            lowband=args.workload.endswith("lowband"))
         return
     if args.workload == "example3-lowband":
         workload_example3(warm=1, nc=57)   # N_s = 112 over T = 0.035 s: Omega ~ 10000 rad/s
