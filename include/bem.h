@@ -438,8 +438,8 @@ int bem_kernel_time(bem_ctx* ctx, int kind, int64_t* launches, double* ms, int64
 
 /* ------------------------------------------------------------------ launch tuning
  * The FP32 far-field launch (the operator's hot loop) has three shape parameters:
- *   ft    frequencies one CTA evaluates together (4, 8 or 12): each source point's geometry is
- *         formed once and reused for them;
+ *   ft    frequencies one CTA evaluates together (1, 4, 8 or 12): each source point's geometry
+ *         is formed once and reused for them;
  *   tiles 32-element source tiles a CTA sums in FP32 before its FP64 atomic add;
  *   waves the source range is split until the grid holds waves x SMs x resident CTAs per SM.
  * The best shape depends on the mesh size and on how many frequencies a launch carries (GMRES
@@ -458,17 +458,19 @@ typedef struct bem_tune_entry {
 
 /* Autotuner: for the context's mesh (material and boundary conditions set), and for launches of
  * the first nfl[j] frequencies of s (j < n_nfl, each <= ns), times one FP32 operator application
- * (far-field launches + near field) for every shape (ft in {4, 8, 12}, tiles in {1, 2, 4}, waves in {2, 4, 8}; CUDA events, best of 2
- * after a warm-up) and keeps the fastest.  out[n_nfl] (host): the chosen entries (ne_max = the
- * mesh's ne).  They are also installed in the context (replacing entries with the same ne_max).
+ * (far-field launches + near field) for every shape (ft in {4, 8, 12}, and 1 for launches of at
+ * most 2 frequencies; tiles in {1, 2, 4}; waves in {2, 4, 8}; CUDA events, best of 2 after a
+ * warm-up) and keeps the fastest.  out[n_nfl] (host): the chosen entries (ne_max = the mesh's
+ * ne).  They are also installed in the context (replacing entries with the same ne_max).
  * Errors: INVALID_ARG (sizes, nfl[j] outside [1, ns]), NO_MESH, OOM, CUDA. */
 int bem_autotune(bem_ctx* ctx, const double* s, int64_t ns, const int32_t* nfl, int32_t n_nfl,
                  bem_tune_entry* out);
 /* Install a table of n entries (host; copied), replacing the context's table; n = 0 restores
- * the fixed shape.  Errors: INVALID_ARG (an entry with ft not 4, 8 or 12, tiles or waves < 1). */
+ * the fixed shape.  Errors: INVALID_ARG (an entry with ft not 1, 4, 8 or 12, tiles or waves < 1). */
 int bem_set_tuning(bem_ctx* ctx, const bem_tune_entry* table, int32_t n);
-/* Read a table from a text file (one entry per line: ne_max nfl_max ft tiles waves [ms ms_fixed]; '#'
- * starts a comment; ms and ms_fixed are optional) and install it.  Errors: INVALID_ARG (unreadable file or bad line). */
+/* Read a table from a text file (one entry per line: ne_max nfl_max ft tiles waves [ms ms_fixed];
+ * '#' starts a comment; ms and ms_fixed are optional) and install it.
+ * Errors: INVALID_ARG (unreadable file or bad line). */
 int bem_load_tuning(bem_ctx* ctx, const char* path);
 /* The shape a far-field launch of nfl frequencies on the context's mesh would use. */
 int bem_launch_shape(bem_ctx* ctx, int64_t nfl, int32_t* ft, int32_t* tiles, int32_t* waves);

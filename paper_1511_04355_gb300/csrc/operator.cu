@@ -856,6 +856,7 @@ static void launch_far_part(bem_ctx* ctx, const cx<R>* x, int which, int64_t off
   if constexpr (sizeof(R) == 4 && !RESID) {
     // the launch shape (frequencies per CTA, tiles per CTA, waves) from the tuning table
     switch (sh.ft) {
+      case 1: launch_far32<1, REC>(ctx, a, ng, sh); break;
       case 4: launch_far32<4, REC>(ctx, a, ng, sh); break;
       case 8: launch_far32<8, REC>(ctx, a, ng, sh); break;
       default: launch_far32<12, REC>(ctx, a, ng, sh); break;

@@ -14,12 +14,12 @@ namespace bem {
 
 namespace {
 
-constexpr int kFts[] = {4, 8, 12};
+constexpr int kFts[] = {1, 4, 8, 12};  // 1 only for launches of at most 2 frequencies
 constexpr int kTiles[] = {1, 2, 4};
 constexpr int kWaves[] = {2, 4, 8};
 
 void check_entry(const bem_tune_entry& e) {
-  BEM_REQUIRE(e.ft == 4 || e.ft == 8 || e.ft == 12, "tuning entry: ft must be 4, 8 or 12");
+  BEM_REQUIRE(e.ft == 1 || e.ft == 4 || e.ft == 8 || e.ft == 12, "tuning entry: ft must be 1, 4, 8 or 12");
   BEM_REQUIRE(e.tiles >= 1 && e.tiles <= 64, "tuning entry: tiles must be in [1, 64]");
   BEM_REQUIRE(e.waves >= 1 && e.waves <= 64, "tuning entry: waves must be in [1, 64]");
   BEM_REQUIRE(e.ne_max >= 1 && e.nfl_max >= 1, "tuning entry: ne_max and nfl_max must be >= 1");
@@ -144,6 +144,7 @@ int bem_autotune(bem_ctx* ctx, const double* s, int64_t ns, const int32_t* nfl, 
         for (int ft : kFts)
           for (int tiles : kTiles)
             for (int waves : kWaves) {
+              if (ft == 1 && nfl[j] > 2) continue;
               ctx->tune_forced = true;
               ctx->tune_force.ft = ft;
               ctx->tune_force.tiles = tiles;
