@@ -19,4 +19,7 @@ Modules
   vf          vector fitting (Sec. 2.3, Eqs. (vf-f), (vf-td))
   afs         adaptive frequency sampling driver (Sec. 3, Eqs. (snew)-(converge), Algorithm AFS)
   mlp         POD basis and the small MLP warm-start model, forward/backward/Adam in FP64
+  hmatrix     hierarchical low-rank far field (the fast matrix-vector product's role, Sec. 2.1):
+              the dense 4-point far field it approximates, cluster tree, block partition,
+              adaptive cross approximation and the H-matrix product
 """
