@@ -742,13 +742,15 @@ def workload_example3(warm=0, n=(12, 12, 18), void_level=1, nc=240):
                max_samples=nc + nc // 3)
 
 
-def workload_large(n_freq=8):
+def workload_large(n_freq=8, hmatrix=None):
     """The large porous solid: a 2 x 1 x 1 m block with 200 seeded spherical voids (radii 0.05-0.1
     m, level-2 icospheres) and 84 x 42 x 42 face grids, 99280 triangles (297840 complex unknowns);
     step traction 1e6 Pa on z = 0, z = 1 fixed.  One batched mixed-precision solve (tol 1e-6,
     GMRES(100)) of the first n_freq frequencies s_k = eta + i k 2 pi / P with P = 40 ms and eta =
     3 ln(10) / P (Sec. 2.2, kappa = 3) through bem_solve_frequencies.  Prints one JSON line with
-    solves/s, GMRES iterations, refinements and the device memory the solve held."""
+    solves/s, GMRES iterations, refinements and the device memory the solve held.  hmatrix: a dict
+    of bem_hmatrix_params fields; the FP32 inner operator then uses the H-matrix far field (the
+    FP64-class residual stays the exact operator)."""
     import torch
 
     import paper_1511_04355_gb300 as P
@@ -765,6 +767,8 @@ def workload_large(n_freq=8):
     c.set_bc(pb["bc_type"], pb["bc_value"], P.BEM_PROFILE_STEP)
     t_setup = time.perf_counter() - t0
     c.set_options(precision=P.BEM_PREC_MIXED, tol=TOL, restart=100, max_iters=3000, max_refine=12)
+    if hmatrix is not None:
+        c.set_hmatrix(True, **hmatrix)
     torch.cuda.synchronize()
     torch.cuda.reset_peak_memory_stats()
     free0, total = torch.cuda.mem_get_info()
@@ -789,6 +793,18 @@ def workload_large(n_freq=8):
                       "tflops_executed": fl32 * ne * (ne - 1) * 4 * FLOPS_EXEC_PER_UNIT_FAR32 / (ms32 / 1e3) / 1e12
                       if ms32 > 0 else None},
             "kernel_ms": {k: v[1] for k, v in kt.items()}}
+    if hmatrix is not None:
+        hi = c.hmatrix_info()
+        line["workload"] += "; H-matrix far field in the FP32 inner operator"
+        line["hmatrix"] = {"params": hmatrix, "info": hi,
+                           "apply": {"launches": kt["happly"][0], "ms": kt["happly"][1],
+                                     "frequency_applies": kt["happly"][2]},
+                           "build_ms": kt["hbuild"][1]}
+        na = kt["happly"][2]
+        if na > 0 and hi["frequencies"] > 0:
+            # the low-rank factors of one frequency, read once per frequency application
+            line["hmatrix"]["factor_bytes_per_frequency"] = hi["factor_bytes"] / hi["frequencies"]
+            line["hmatrix"]["ms_per_frequency_apply"] = kt["happly"][1] / na
     print(json.dumps(line), flush=True)
 
 
@@ -806,12 +822,16 @@ def main():
                     help="warm start of the AFS solves in the AFS-vs-FSM workloads (default nearest)")
     ap.add_argument("--afs-tol", type=float, default=AFS_TOL,
                     help="residual tolerance of the AFS samples in the AFS-vs-FSM workloads")
+    ap.add_argument("--hm-eps", type=float, default=1e-4,
+                    help="cross-approximation tolerance of the H-matrix workloads")
+    ap.add_argument("--hm-max-freqs", type=int, default=2,
+                    help="frequencies whose H-matrix factors are held at once (H-matrix workloads)")
     ap.add_argument("--kernel-case-single", action="store_true",
                     help="run only the single-frequency FP32 operator case used for ncu captures")
     ap.add_argument("--profile-step", action="store_true",
                     help="run one benchmark solve with kernel counts (for ncu instruction counters)")
     ap.add_argument("--workload", choices=["uneven", "porous-afs", "porous-afs-full", "example3",
-                                           "example3-mlp", "large", "porous-afs-lowband",
+                                           "example3-mlp", "large", "large-hmatrix", "porous-afs-lowband",
                                            "porous-afs-full-lowband", "example3-lowband"],
                     help="run one of the other workloads instead of the benchmark (own JSON line)")
     args = ap.parse_args()
@@ -839,6 +859,9 @@ def main():
         return
     if args.workload == "large":
         workload_large()
+    if args.workload == "large-hmatrix":
+        workload_large(hmatrix=dict(leaf=32, eta=2.0, max_block=512, max_rank=128, eps=args.hm_eps,
+                                    max_freqs=args.hm_max_freqs))
         return
     if args.workload in ("example3", "example3-mlp"):
         workload_example3(warm=2 if args.workload == "example3-mlp" else 1)

@@ -425,6 +425,8 @@ int bem_precond_apply(bem_ctx* ctx, const double* s, int64_t ns, const double* x
 #define BEM_KERNEL_SELF 4    /* own-element singular blocks + preconditioner       */
 #define BEM_KERNEL_VEC 5     /* GMRES vector kernels of one Arnoldi step            */
 #define BEM_KERNEL_RES64 6   /* FP64 residual r = K k - A x (far field, fused U + T) */
+#define BEM_KERNEL_HAPPLY 7  /* H-matrix far field: low-rank and dense blocks applied    */
+#define BEM_KERNEL_HBUILD 8  /* H-matrix build: cross approximations and factor copies   */
 
 /* Enable (1) or disable (0) CUDA-event timing of the kernel classes above, on the context's
  * stream; resets the totals.  Timing adds two event records per timed launch. */
@@ -488,6 +490,82 @@ int bem_launch_shape(bem_ctx* ctx, int64_t nfl, int32_t* ft, int32_t* tiles, int
 #define BEM_PEAK_FP32X2 2  /* FP32 with the paired instruction (two FMAs per thread per FFMA2) */
 int bem_measure_peak(bem_ctx* ctx, int kind, int32_t iters, int32_t reps, double* tflops,
                      double* ms_best, int32_t* sm_count);
+
+/* ------------------------------------------------------------------ fast far field (H-matrix)
+ *
+ * The paper speeds up the matrix-vector product of its iterative solve with a fast multipole
+ * method (Sec. 2.1, the paragraph on the fast solver).  This library's fast far field is a
+ * hierarchical matrix of the 4-point-rule far-field part A4 of the system operator,
+ *     A4[i, e] = sum_q w_q K_e(x_i, y_q)  for e != i  (K_e = T for a traction-given column,
+ *                -U for a displacement-given one),   A4[i, i] = 0,
+ * the part the FP32 far kernel sums over all sources; the near-field and own-element
+ * corrections are applied exactly as without it.  The elements are ordered by a cluster tree
+ * (recursive median bisection along the longest side of the centroids' bounding box, ties by
+ * element index, first half = size / 2 to the left, until at most `leaf` elements).  A pair of
+ * clusters whose vertex bounding boxes satisfy max(diam) <= eta dist, dist > 0, and whose sizes
+ * are at most max_block, is a low-rank block (U V^T from a partially pivoted cross approximation
+ * to the relative Frobenius tolerance eps, with trial steps from each vector component before it
+ * stops, displacement-given columns scaled by mu / D inside it, D the mesh's bounding-box
+ * diagonal; FP32 factors); a pair of leaves that is not is a dense block, evaluated on the fly.
+ * Other pairs are split, both sides (the non-leaf side when one is a leaf), depth first.
+ *
+ * When enabled, every FP32 application of A (the inner GMRES operator of BEM_PREC_MIXED solves
+ * and bem_apply with BEM_PREC_FP32, BEM_APPLY_A) uses it.  The factors are built on the device
+ * at the first such application after the frequency set changes, for all frequencies of the
+ * set.  The FP64-class refinement residual stays the exact operator, so a mixed solve still
+ * certifies tol against the full discretisation; the approximation only changes how many
+ * refinements it takes. */
+typedef struct bem_hmatrix_params {
+  int32_t enable;     /* 1: use the H-matrix far field; 0: the direct far kernel (default 0)  */
+  int32_t leaf;       /* elements per leaf cluster, at most (default 32; 1 .. 128)            */
+  int32_t max_block;  /* elements per side of a low-rank block, at most (default 512;
+                         leaf .. 1024)                                                        */
+  int32_t max_rank;   /* rank cap of one block's cross approximation (default 96; 1 .. 256);
+                         a block that reaches it keeps that rank and is counted in `capped`  */
+  double eta;         /* admissibility parameter (default 2.0; > 0)                           */
+  double eps;         /* cross-approximation tolerance (default 1e-4; 0 < eps < 1)            */
+  int32_t max_freqs;  /* frequencies whose factors are held at once: a bem_solve_frequencies
+                         or bem_fsm list longer than this is solved in consecutive chunks of
+                         max_freqs frequencies (default 0: the whole list at once)           */
+  int32_t reserved[5];
+} bem_hmatrix_params;
+
+typedef struct bem_hmatrix_info {
+  int64_t clusters;        /* clusters of the tree                                          */
+  int64_t lowrank_blocks;  /* low-rank blocks of the partition                              */
+  int64_t dense_blocks;    /* dense blocks                                                  */
+  int64_t lowrank_pairs;   /* element pairs the low-rank blocks cover                       */
+  int64_t dense_pairs;     /* element pairs the dense blocks cover (the on-the-fly work)    */
+  int64_t frequencies;     /* frequencies of the last build                                */
+  int64_t factor_bytes;    /* device bytes of the factors of the last build                 */
+  int64_t rank_sum;        /* sum of the block ranks over blocks and frequencies            */
+  int32_t rank_max;        /* largest block rank                                            */
+  int32_t capped;          /* (block, frequency) approximations that reached max_rank       */
+  double seconds_build;    /* wall time of the last build (cross approximations + copies)   */
+  int64_t builds;          /* builds since the parameters were set                          */
+  int64_t reserved[4];
+} bem_hmatrix_info;
+
+/* Defaults of bem_hmatrix_params (enable = 0). */
+int bem_default_hmatrix_params(bem_hmatrix_params* p);
+/* Enable (p->enable = 1), disable (p->enable = 0 or p NULL) or re-parametrise the H-matrix far
+ * field; drops any factors held.  Errors: INVALID_ARG (a parameter out of range). */
+int bem_set_hmatrix(bem_ctx* ctx, const bem_hmatrix_params* p);
+/* Statistics of the partition and of the last build (host struct). */
+int bem_get_hmatrix_info(bem_ctx* ctx, bem_hmatrix_info* out);
+/* The cluster tree and block partition the H-matrix uses for a mesh (host only, no context and
+ * no GPU needed).  verts: nv x 3 doubles, tris: ne x 3 int32 (host).  Outputs (host, each
+ * nullable): perm[ne] (tree position -> element), clusters[cap_clusters][2] (first position,
+ * size) in depth-first order (a cluster, its left subtree, its right subtree), lowrank and
+ * dense [cap][2] (target cluster, source cluster) in the order of the depth-first subdivision
+ * of (root, root), target children outer.  counts[3] (host, required) receives the numbers of
+ * clusters, low-rank and dense blocks; an array whose capacity is smaller is not written.
+ * Errors: INVALID_ARG (sizes, indices or parameters out of range); message in
+ * bem_last_error(NULL). */
+int bem_hmatrix_partition(const double* verts, int64_t nv, const int32_t* tris, int64_t ne,
+                          const bem_hmatrix_params* p, int32_t* perm, int32_t* clusters,
+                          int64_t cap_clusters, int32_t* lowrank, int64_t cap_lowrank,
+                          int32_t* dense, int64_t cap_dense, int64_t* counts);
 
 #ifdef __cplusplus
 }

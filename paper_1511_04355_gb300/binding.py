@@ -47,11 +47,13 @@ BEM_KERNEL_NEAR64 = 3
 BEM_KERNEL_SELF = 4
 BEM_KERNEL_VEC = 5
 BEM_KERNEL_RES64 = 6
+BEM_KERNEL_HAPPLY = 7
+BEM_KERNEL_HBUILD = 8
 BEM_PEAK_FP32 = 0
 BEM_PEAK_FP64 = 1
 BEM_PEAK_FP32X2 = 2
 KERNEL_NAMES = {0: "far32", 1: "far64", 2: "near32", 3: "near64", 4: "self", 5: "gmres_vec",
-                6: "res64"}
+                6: "res64", 7: "happly", 8: "hbuild"}
 
 
 class BemError(RuntimeError):
@@ -108,6 +110,20 @@ class bem_tune_entry(C.Structure):
                 ("ms_fixed", C.c_double)]
 
 
+class bem_hmatrix_params(C.Structure):
+    _fields_ = [("enable", C.c_int32), ("leaf", C.c_int32), ("max_block", C.c_int32),
+                ("max_rank", C.c_int32), ("eta", C.c_double), ("eps", C.c_double),
+                ("max_freqs", C.c_int32), ("reserved", C.c_int32 * 5)]
+
+
+class bem_hmatrix_info(C.Structure):
+    _fields_ = [("clusters", C.c_int64), ("lowrank_blocks", C.c_int64), ("dense_blocks", C.c_int64),
+                ("lowrank_pairs", C.c_int64), ("dense_pairs", C.c_int64), ("frequencies", C.c_int64),
+                ("factor_bytes", C.c_int64), ("rank_sum", C.c_int64), ("rank_max", C.c_int32),
+                ("capped", C.c_int32), ("seconds_build", C.c_double), ("builds", C.c_int64),
+                ("reserved", C.c_int64 * 4)]
+
+
 class bem_batch_item(C.Structure):
     _fields_ = [("ctx", C.c_void_p), ("s", C.c_void_p), ("ns", C.c_int64), ("x_out", C.c_void_p),
                 ("stats", C.POINTER(bem_solve_stats)), ("status", C.c_int32)]
@@ -162,6 +178,11 @@ _SIGS = {
     "bem_load_tuning": (C.c_int, [_P, C.c_char_p]),
     "bem_launch_shape": (C.c_int, [_P, _I64, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int32)]),
+    "bem_default_hmatrix_params": (C.c_int, [C.POINTER(bem_hmatrix_params)]),
+    "bem_set_hmatrix": (C.c_int, [_P, C.POINTER(bem_hmatrix_params)]),
+    "bem_get_hmatrix_info": (C.c_int, [_P, C.POINTER(bem_hmatrix_info)]),
+    "bem_hmatrix_partition": (C.c_int, [_P, _I64, _P, _I64, C.POINTER(bem_hmatrix_params), _P, _P, _I64,
+                                        _P, _I64, _P, _I64, _P]),
 }
 
 _lib = None
@@ -666,6 +687,46 @@ def bem_measure_peak(ctx, kind, iters=2048, reps=5):
     return tf.value, ms.value, sm.value
 
 
+def bem_default_hmatrix_params(**kw):
+    p = bem_hmatrix_params()
+    _check_global(load_library().bem_default_hmatrix_params(C.byref(p)), "bem_default_hmatrix_params")
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(f"bem_hmatrix_params has no field {k}")
+        setattr(p, k, v)
+    return p
+
+
+def bem_set_hmatrix(ctx, params=None):
+    _check(ctx, load_library().bem_set_hmatrix(ctx, C.byref(params) if params is not None else None),
+           "bem_set_hmatrix")
+
+
+def bem_get_hmatrix_info(ctx):
+    out = bem_hmatrix_info()
+    _check(ctx, load_library().bem_get_hmatrix_info(ctx, C.byref(out)), "bem_get_hmatrix_info")
+    return {name: getattr(out, name) for name, _ in bem_hmatrix_info._fields_ if name != "reserved"}
+
+
+def bem_hmatrix_partition(verts, tris, params=None):
+    """(perm, clusters (n, 2), lowrank (n, 2), dense (n, 2)) of the H-matrix tree and partition."""
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    p = params if params is not None else bem_default_hmatrix_params()
+    lib = load_library()
+    counts = np.zeros(3, np.int64)
+    perm = np.zeros(len(t), np.int32)
+    _check_global(lib.bem_hmatrix_partition(_ptr(v), len(v), _ptr(t), len(t), C.byref(p), _ptr(perm), None, 0,
+                                            None, 0, None, 0, _ptr(counts)), "bem_hmatrix_partition")
+    cl = np.zeros((max(int(counts[0]), 1), 2), np.int32)
+    lr = np.zeros((max(int(counts[1]), 1), 2), np.int32)
+    dn = np.zeros((max(int(counts[2]), 1), 2), np.int32)
+    _check_global(lib.bem_hmatrix_partition(_ptr(v), len(v), _ptr(t), len(t), C.byref(p), _ptr(perm), _ptr(cl),
+                                            int(counts[0]), _ptr(lr), int(counts[1]), _ptr(dn), int(counts[2]),
+                                            _ptr(counts)), "bem_hmatrix_partition")
+    return perm, cl[:counts[0]], lr[:counts[1]], dn[:counts[2]]
+
+
 class Context:
     """Owns one bem_ctx (device + stream) and remembers the mesh size.  tuning: a launch-shape
     table file to load (True: the table written by paper_1511_04355_gb300.tune, when it exists;
@@ -726,6 +787,14 @@ class Context:
 
     def profile(self, enable=True):
         bem_profile(self.h, enable)
+
+    def set_hmatrix(self, enable=True, **kw):
+        """Enable (or disable) the H-matrix far field of the FP32 operator; kw: fields of
+        bem_hmatrix_params (leaf, max_block, max_rank, eta, eps, max_freqs)."""
+        bem_set_hmatrix(self.h, bem_default_hmatrix_params(enable=int(enable), **kw))
+
+    def hmatrix_info(self):
+        return bem_get_hmatrix_info(self.h)
 
     def kernel_times(self):
         """{name: (launches, milliseconds, frequency-launches)} since profile(True)."""

@@ -33,8 +33,13 @@ def sources():
                   if f.endswith(".cu") or f.endswith(".cpp"))
 
 
+# Per-file host flags: the H-matrix cluster tree compares coordinates and distances, and must
+# round every product and sum separately on every host architecture (no fused multiply-add).
+FILE_FLAGS = {"hmatrix_tree.cpp": ["-Xcompiler", "-ffp-contract=off"]}
+
+
 def _compile(src, obj, extra):
-    cmd = [nvcc(), *ARCH, *CFLAGS, *extra, "-c", src, "-o", obj]
+    cmd = [nvcc(), *ARCH, *CFLAGS, *FILE_FLAGS.get(os.path.basename(src), []), *extra, "-c", src, "-o", obj]
     p = subprocess.run(cmd, capture_output=True, text=True)
     return src, p.returncode, p.stdout + p.stderr
 

@@ -163,9 +163,26 @@ void solve_frequency_list(bem_ctx* ctx, const double* sh, int64_t ns, cx<double>
   if (wmode != BEM_WARM_SWEEP || ns < 8) {
     const int saved = ctx->opt.warm_start;
     if (wmode == BEM_WARM_SWEEP) ctx->opt.warm_start = BEM_WARM_ZERO;
-    prepare_frequencies(ctx, sh, ns, mixed);
+    // with the H-matrix far field, at most max_freqs frequencies' factors at a time
+    const int64_t chunk = hm_active(ctx) && ctx->hm.prm.max_freqs > 0 ? ctx->hm.prm.max_freqs : ns;
+    it.assign(ns, 0);
+    rf.assign(ns, 0);
+    res.assign(ns, 0.0);
+    status.assign(ns, 0);
     try {
-      solve_batch(ctx, x_dev, nullptr, it, rf, res, status);
+      for (int64_t c0 = 0; c0 < ns; c0 += chunk) {
+        const int64_t nc = std::min(chunk, ns - c0);
+        prepare_frequencies(ctx, sh + 2 * c0, nc, mixed);
+        std::vector<int32_t> it_c, rf_c, st_c;
+        std::vector<double> res_c;
+        solve_batch(ctx, x_dev + c0 * 3 * ctx->mesh.ne, nullptr, it_c, rf_c, res_c, st_c);
+        for (int64_t k = 0; k < nc; ++k) {
+          it[c0 + k] = it_c[k];
+          rf[c0 + k] = rf_c[k];
+          res[c0 + k] = res_c[k];
+          status[c0 + k] = st_c[k];
+        }
+      }
     } catch (...) {
       ctx->opt.warm_start = saved;
       throw;

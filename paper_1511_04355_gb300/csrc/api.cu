@@ -249,6 +249,7 @@ int bem_set_mesh(bem_ctx* ctx, const double* verts, int64_t nv, const int32_t* t
                        (hi[2] - lo[2]) * (hi[2] - lo[2]));
     ctx->bc.set = false;
     ctx->fs.valid = false;
+    hm_invalidate(ctx, true);
     try {
       build_geometry(ctx);
       build_near_lists(ctx);
@@ -269,6 +270,7 @@ int bem_set_material(bem_ctx* ctx, double mu, double nu, double rho) {
     ctx->mat.rho = rho;
     ctx->mat.set = true;
     ctx->fs.valid = false;
+    hm_invalidate(ctx, false);
   });
 }
 
@@ -291,6 +293,7 @@ int bem_set_bc(bem_ctx* ctx, const int8_t* type, const double* value, int profil
     copy_in(ctx, b.d_value.p, b.value.data(), sizeof(double) * 3 * ne);
     b.set = true;
     ctx->fs.valid = false;
+    hm_invalidate(ctx, false);
   });
 }
 

@@ -14,11 +14,13 @@
 
 #include <cmath>
 #include <cstdio>
+#include <memory>
 #include <stdexcept>
 #include <string>
 #include <vector>
 
 #include "../../include/bem.h"
+#include "hmatrix_host.h"
 
 namespace bem {
 
@@ -225,7 +227,7 @@ struct FreqSet {
 };
 
 // Optional CUDA-event timing of kernel classes (enabled by bem_profile).
-enum ProfKind { PK_FAR32 = 0, PK_FAR64, PK_NEAR32, PK_NEAR64, PK_SELF, PK_VEC, PK_RES64, PK_COUNT };
+enum ProfKind { PK_FAR32 = 0, PK_FAR64, PK_NEAR32, PK_NEAR64, PK_SELF, PK_VEC, PK_RES64, PK_HAPPLY, PK_HBUILD, PK_COUNT };
 struct ProfRec {
   int kind;
   cudaEvent_t a, b;
@@ -250,6 +252,31 @@ struct WarmStart {
   int64_t vf_J = 0;
 };
 
+// H-matrix far field (hmatrix.cu): structure of the current mesh and parameters, and the
+// FP32 low-rank factors of the current frequency set.
+struct HMat {
+  bem_hmatrix_params prm{};     // enable = 0: off
+  bool have_structure = false;  // tree, partition and their device copies are current
+  hm::Tree tree;
+  hm::Partition part;
+  DevBuf perm;                  // int32[ne]: tree position -> element
+  DevBuf lr;                    // int4[n_lr]: low-rank block (t0, tn, s0, sn) as tree positions
+  DevBuf tgrp;                  // int4[n_tg]: target cluster (t0, tn, first, count) of tblk
+  DevBuf tblk;                  // int32[n_lr]: low-rank blocks grouped by target cluster
+  DevBuf dgrp;                  // int4[n_dg]: target leaf (t0, tn, first, count) of dsrc
+  DevBuf dsrc;                  // int2[n_dn]: dense blocks' source leaves (s0, sn), grouped
+  int64_t n_lr = 0, n_tg = 0, n_dg = 0, n_dn = 0, lr_pairs = 0, dn_pairs = 0;
+  int max_lr = 0;               // largest side (elements) of a low-rank block
+  int max_leaf = 0;             // largest leaf
+  bool built = false;           // factors for the current frequency set
+  int64_t F = 0;
+  DevBuf rank;                  // int32[F][n_lr]
+  DevBuf fptr;                  // (float2*)[F][n_lr]: U (3 tn x k) then V (3 sn x k) of a block
+  std::vector<std::unique_ptr<DevBuf>> chunks;  // factor storage
+  DevBuf scratch, items, dst, capped, brank;
+  bem_hmatrix_info info{};
+};
+
 }  // namespace bem
 
 struct bem_ctx {
@@ -263,6 +290,7 @@ struct bem_ctx {
   bem::BC bc;
   bem::FreqSet fs;
   bem::WarmStart warm;
+  bem::HMat hm;
   // scratch buffers for vectors (grow-only)
   bem::DevBuf io_a, io_b;       // staging for ABI copies
   bem::DevBuf io_c, io_d, io_e; // staging for the FSM calls (samples, times, output, dofs)
@@ -357,6 +385,14 @@ void solve_frequency_list(bem_ctx* ctx, const double* s_host, int64_t ns, cx<dou
 
 // tune.cu: the shape of an FP32 far-field launch of nfl frequencies on the context's mesh
 FarShape far32_shape(bem_ctx* ctx, int64_t nfl);
+
+// hmatrix.cu: H-matrix far field.  hm_active: enabled for the context's mesh.  hm_far32: the
+// far-field sums of the listed (staged) frequencies into the FP64 accumulator, building the
+// factors first when the frequency set changed.  hm_invalidate: drop the factors (and, with
+// structure = true, the tree and partition).
+bool hm_active(bem_ctx* ctx);
+void hm_far32(bem_ctx* ctx, const cx<float>* x, int64_t nfl);
+void hm_invalidate(bem_ctx* ctx, bool structure);
 
 // fsm.cu
 void fsm_check_args(int64_t nc, int64_t m, double eta, double period, int64_t nt, int window);

@@ -574,6 +574,7 @@ __global__ void self_blocks_kernel(SelfArgs a) {
 
 // ------------------------------------------------------------------------------- frequencies
 void prepare_frequencies(bem_ctx* ctx, const double* s, int64_t F, bool df_self) {
+  hm_invalidate(ctx, false);  // H-matrix factors belong to the previous frequency set
   Mesh& me = ctx->mesh;
   FreqSet& fs = ctx->fs;
   const MatC<double> m = mat_constants64(ctx->mat);

@@ -61,56 +61,6 @@ __device__ __forceinline__ float column_code(const int8_t* bc, int64_t e, int wh
   return sign * (useU ? 2.f : 1.f);
 }
 
-// Source-target distance.  FP32: float-float difference of the float-float coordinates and a
-// float-float |d|^2, so that r carries ~1e-9 relative error (the phase omega r / c reaches ~60 rad
-// at the top of the band); rh, dr/dn and the weights only need single precision.  FP64: plain.
-template <class R>
-struct Dist {
-  R dx, dy, dz, r, r_lo, rinv;
-};
-
-// Knuth's TwoSum, s + e = a + b exactly; the intrinsics keep the compiler from contracting the
-// products of the squared distance into these sums.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-__device__ __forceinline__ Dist<float> distance(float px, float py, float pz, float4 pl, float x0,
-                                                float x1, float x2, float4 xl, bool self) {
-  Dist<float> d;
-  float ex, ey, ez;
-  two_sum(px, -x0, d.dx, ex);
-  two_sum(py, -x1, d.dy, ey);
-  two_sum(pz, -x2, d.dz, ez);
-  const float lx = ex + (pl.x - xl.x), ly = ey + (pl.y - xl.y), lz = ez + (pl.z - xl.z);
-  const float sx = d.dx * d.dx, sy = d.dy * d.dy, sz = d.dz * d.dz;
-  const float qx = fmaf(d.dx, d.dx, -sx), qy = fmaf(d.dy, d.dy, -sy), qz = fmaf(d.dz, d.dz, -sz);
-  float s1, e1, s2, e2;
-  two_sum(sx, sy, s1, e1);
-  two_sum(s1, sz, s2, e2);
-  const float lo = (e1 + e2) + (qx + qy + qz) + 2.f * (d.dx * lx + d.dy * ly + d.dz * lz);
-  if (self) s2 = 1.f;
-  d.rinv = rsqrtf(s2);
-  d.r = s2 * d.rinv;
-  d.r_lo = self ? 0.f : (fmaf(-d.r, d.r, s2) + lo) * 0.5f * d.rinv;
-  return d;
-}
-
-__device__ __forceinline__ Dist<double> distance(double px, double py, double pz, float4, double x0,
-                                                 double x1, double x2, float4, bool self) {
-  Dist<double> d;
-  d.dx = px - x0;
-  d.dy = py - x1;
-  d.dz = pz - x2;
-  const double r2 = self ? 1.0 : d.dx * d.dx + d.dy * d.dy + d.dz * d.dz;
-  d.rinv = rsqrt(r2);
-  d.r = r2 * d.rinv;
-  d.r_lo = 0.0;
-  return d;
-}
-
 // T-kernel contribution of one source point to the three output components:
 //   o_c += cw [A (dr/dn v_c + (rh.v) n_c) + rh_c (q1 (n.v) + q2 dr/dn (rh.v))]
 template <class R>
@@ -950,6 +900,15 @@ void residual64(bem_ctx* ctx, const cx<double>* x, cx<double>* r, const std::vec
 
 void apply_operator32(bem_ctx* ctx, const cx<float>* x, cx<float>* y, int which,
                       const std::vector<int32_t>* flist) {
+  if (which == BEM_APPLY_A && hm_active(ctx)) {
+    // H-matrix far field (hmatrix.cu) in place of the direct far kernel
+    const int64_t n = stage_flist(ctx, flist, 0);
+    if (!n) return;
+    hm_far32(ctx, x, n);
+    launch_near<float>(ctx, x, y, which, n, false);
+    ctx->f32_applies++;
+    return;
+  }
   const FarShape sh = far32_shape(ctx, flist ? (int64_t)flist->size() : ctx->fs.F);
   const int64_t n = stage_flist(ctx, flist, sh.ft);
   if (!n) return;

@@ -168,3 +168,41 @@ def test_hmatrix_product_matches_the_dense_far_field(eps):
     lr, dn, full = HM.storage(H)
     if eps >= 1e-3:   # on 480 elements the blocks are small: compression shows at the looser tolerance
         assert lr < 0.8 * (full - dn)
+
+
+def _lib_or_skip():
+    import paper_1511_04355_gb300 as P
+    try:
+        P.load_library()
+    except ImportError:
+        pytest.skip("library not built (run __graft_entry__.build())")
+    return P
+
+
+def test_library_partition_is_the_oracles():
+    P = _lib_or_skip()
+    cav = W.spherical_cavity(level=3, n_freq=2)
+    v1, f1, _, _ = _small_block()
+    rod = W.prismatic_rod(n=(12, 4, 4))
+    for v, f in [(cav.verts, cav.tris), (v1, f1), (rod["verts"], rod["tris"])]:
+        for leaf, eta, mb in [(32, 2.0, 512), (16, 1.0, 64), (7, 3.0, 1024)]:
+            p = P.bem_default_hmatrix_params(leaf=leaf, eta=eta, max_block=mb)
+            perm, cl, lr, dn = P.bem_hmatrix_partition(v, f, p)
+            t = HM.cluster_tree(v, f, leaf)
+            part = HM.block_partition(t, eta, mb)
+            assert np.array_equal(perm, t.perm)
+            assert np.array_equal(cl[:, 0], t.begin) and np.array_equal(cl[:, 1], t.size)
+            assert np.array_equal(lr, part.lowrank) and np.array_equal(dn, part.dense)
+
+
+def test_library_partition_refuses_bad_arguments():
+    P = _lib_or_skip()
+    v, f, _, _ = _small_block()
+    for kw in (dict(leaf=0), dict(leaf=200), dict(max_block=8, leaf=16), dict(eta=0.0), dict(eps=1.5),
+               dict(max_rank=0), dict(max_rank=300), dict(max_freqs=-1)):
+        with pytest.raises(P.BemError):
+            P.bem_hmatrix_partition(v, f, P.bem_default_hmatrix_params(**kw))
+    bad = np.array(f, dtype=np.int32).copy()
+    bad[0, 0] = len(v)
+    with pytest.raises(P.BemError):
+        P.bem_hmatrix_partition(v, bad)
