@@ -523,7 +523,9 @@ typedef struct bem_hmatrix_params {
   int32_t max_rank;   /* rank cap of one block's cross approximation (default 96; 1 .. 256);
                          a block that reaches it keeps that rank and is counted in `capped`  */
   double eta;         /* admissibility parameter (default 2.0; > 0)                           */
-  double eps;         /* cross-approximation tolerance (default 1e-4; 0 < eps < 1)            */
+  double eps;         /* cross-approximation tolerance (default 1e-4; 0 < eps < 1); the factors
+                         and the residuals of the approximation are FP32, so tolerances below
+                         ~1e-5 reach their rounding floor and blocks run to max_rank (capped) */
   int32_t max_freqs;  /* frequencies whose factors are held at once: a bem_solve_frequencies
                          or bem_fsm list longer than this is solved in consecutive chunks of
                          max_freqs frequencies (default 0: the whole list at once)           */

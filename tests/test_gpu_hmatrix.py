@@ -75,7 +75,7 @@ def test_partition_statistics_match_the_host_partition():
     assert info["lowrank_pairs"] == int((sizes[lr[:, 0]] * sizes[lr[:, 1]]).sum())
 
 
-@pytest.mark.parametrize("n,voids,eps", [(4, 2, 1e-4), (8, 6, 1e-4), (8, 6, 1e-6), (16, 10, 1e-4)])
+@pytest.mark.parametrize("n,voids,eps", [(4, 2, 1e-4), (8, 6, 1e-4), (8, 6, 1e-5), (16, 10, 1e-4)])
 def test_hmatrix_apply_matches_the_oracle_operator(n, voids, eps):
     P = _P()
     pb = _block(n, voids)
