@@ -742,6 +742,32 @@ def workload_example3(warm=0, n=(12, 12, 18), void_level=1, nc=240):
                max_samples=nc + nc // 3)
 
 
+def hm_kernel_case():
+    """The H-matrix apply at capture size: a 2 x 1 x 1 m porous block, 32 x 16 x 16 face grids and
+    10 voids (level-1 icospheres, 5920 triangles; about 1 GB of factors, several times the L2),
+    the FP32 operator applied at one frequency (k = 7 of the large workload's list) with the
+    H-matrix far field, twice (the first call builds the factors).  Prints the partition and
+    factor sizes."""
+    import paper_1511_04355_gb300 as P
+
+    pb = W.porous_block(L=(2.0, 1.0, 1.0), n=(32, 16, 16), n_voids=10, radii=(0.08, 0.1), void_level=1)
+    period = 2 * T_WIN
+    s = np.array([3.0 * math.log(10.0) / period + 1j * 7 * 2.0 * math.pi / period])
+    c = P.Context(0)
+    c.set_mesh(pb["verts"], pb["tris"])
+    m = pb["material"]
+    c.set_material(m.mu, m.nu, m.rho)
+    c.set_bc(pb["bc_type"], pb["bc_value"], P.BEM_PROFILE_STEP)
+    c.set_hmatrix(True, leaf=32, eta=2.0, max_block=512, max_rank=128, eps=1e-4)
+    rng = np.random.default_rng(W.SEED)
+    x = rng.standard_normal((1, 3 * len(pb["tris"]))) + 1j * rng.standard_normal((1, 3 * len(pb["tris"])))
+    c.apply(s, x, precision=P.BEM_PREC_FP32)
+    c.profile(True)
+    c.apply(s, x, precision=P.BEM_PREC_FP32)
+    kt = c.kernel_times()
+    print(json.dumps({"triangles": len(pb["tris"]), "info": c.hmatrix_info(), "happly_ms": kt["happly"][1]}))
+
+
 def workload_large(n_freq=8, hmatrix=None):
     """The large porous solid: a 2 x 1 x 1 m block with 200 seeded spherical voids (radii 0.05-0.1
     m, level-2 icospheres) and 84 x 42 x 42 face grids, 99280 triangles (297840 complex unknowns);
@@ -826,6 +852,8 @@ def main():
                     help="cross-approximation tolerance of the H-matrix workloads")
     ap.add_argument("--hm-max-freqs", type=int, default=2,
                     help="frequencies whose H-matrix factors are held at once (H-matrix workloads)")
+    ap.add_argument("--hm-kernel-case", action="store_true",
+                    help="run only the H-matrix apply case used for ncu captures")
     ap.add_argument("--kernel-case-single", action="store_true",
                     help="run only the single-frequency FP32 operator case used for ncu captures")
     ap.add_argument("--profile-step", action="store_true",
@@ -856,6 +884,9 @@ def main():
         return
     if args.workload == "example3-lowband":
         workload_example3(warm=1, nc=57)   # N_s = 112 over T = 0.035 s: Omega ~ 10000 rad/s
+        return
+    if args.hm_kernel_case:
+        hm_kernel_case()
         return
     if args.workload == "large":
         workload_large()

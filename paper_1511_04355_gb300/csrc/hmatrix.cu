@@ -484,6 +484,7 @@ __global__ void __launch_bounds__(kApplyThreads) lowrank_apply_kernel(const LowR
     for (int l = warp; l < k; l += kApplyThreads / 32) {
       cx<float> acc = mk(0.f, 0.f);
       const float2* v = V + (int64_t)l * N;
+#pragma unroll 4
       for (int j = lane; j < N; j += 32) {
         const float2 w = v[j];
         acc = cfma(mk(w.x, w.y), xs[j], acc);
@@ -494,6 +495,7 @@ __global__ void __launch_bounds__(kApplyThreads) lowrank_apply_kernel(const LowR
     __syncthreads();
     for (int i = tid; i < M; i += kApplyThreads) {
       cx<float> acc = ys[i];
+#pragma unroll 4
       for (int l = 0; l < k; ++l) {
         const float2 u = U[(int64_t)l * M + i];
         acc = cfma(mk(u.x, u.y), ts[l], acc);
