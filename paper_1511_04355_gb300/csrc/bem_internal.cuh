@@ -261,9 +261,9 @@ struct HMat {
   hm::Partition part;
   DevBuf perm;                  // int32[ne]: tree position -> element
   DevBuf lr;                    // int4[n_lr]: low-rank block (t0, tn, s0, sn) as tree positions
-  DevBuf tgrp;                  // int4[n_tg]: target cluster (t0, tn, first, count) of tblk
+  DevBuf tgrp;                  // int4[n_tg]: target cluster (t0, tn, first, count <= 4) of tblk
   DevBuf tblk;                  // int32[n_lr]: low-rank blocks grouped by target cluster
-  DevBuf dgrp;                  // int4[n_dg]: target leaf (t0, tn, first, count) of dsrc
+  DevBuf dgrp;                  // int4[n_dg]: target leaf (t0, tn, first, count <= 4) of dsrc
   DevBuf dsrc;                  // int2[n_dn]: dense blocks' source leaves (s0, sn), grouped
   int64_t n_lr = 0, n_tg = 0, n_dg = 0, n_dn = 0, lr_pairs = 0, dn_pairs = 0;
   int max_lr = 0;               // largest side (elements) of a low-rank block

@@ -9,11 +9,11 @@
 //     fly in FP32 with float-float source-target distances, factors written to a scratch area;
 //   * copy_factors_kernel: moves each block's U (3 m x k) and V (3 n x k) into exactly sized
 //     storage, undoing the column scaling of displacement-given columns;
-//   * lowrank_apply_kernel: one CTA per (target cluster, frequency): for each of the cluster's
-//     low-rank blocks t = V^T x_sigma (a warp per rank), y_tau += U t, then one FP64 atomic add
-//     per output into the far-field accumulator;
-//   * dense_apply_kernel: one CTA per (target leaf, frequency): the leaf's dense (inadmissible)
-//     source leaves summed on the fly with the 4-point rule, own element excluded.
+//   * lowrank_apply_kernel: one CTA per (group of up to 4 low-rank blocks of one target cluster,
+//     frequency): per block t = V^T x_sigma (a warp per rank), y_tau += U t, then one FP64
+//     atomic add per output into the far-field accumulator;
+//   * dense_apply_kernel: one CTA per (group of up to 4 dense source leaves of one target leaf,
+//     frequency): summed on the fly with the 4-point rule, own element excluded.
 // The near-field and own-element corrections of the FP32 operator then run unchanged.  The
 // low-rank apply reads each factor once per application (HBM-bound); the dense part is bound by
 // the FP32 kernel arithmetic like the direct far kernel.
@@ -29,6 +29,7 @@ constexpr int kHMaxRank = 256;   // bound of max_rank (shared-memory arrays of t
 constexpr int kAcaThreads = 128;
 constexpr int kApplyThreads = 256;
 constexpr int kDenseThreads = 128;
+constexpr int64_t kGroupBlocks = 4;  // blocks (low-rank) or source leaves (dense) per apply CTA
 
 struct HGeo {
   const float4* q4;    // [ne][4] (x, y, z, w * area)
@@ -458,8 +459,8 @@ struct LowRankArgs {
   int nmax;
 };
 
-// One CTA per (target cluster, listed frequency): the sum over the cluster's low-rank blocks of
-// U (V^T x_sigma), accumulated in shared memory, then added to the FP64 far-field sums.
+// One CTA per (group of a target cluster's low-rank blocks, listed frequency): the sum over the
+// group of U (V^T x_sigma), accumulated in shared memory, then added to the FP64 far-field sums.
 __global__ void __launch_bounds__(kApplyThreads) lowrank_apply_kernel(const LowRankArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<float>* xs = reinterpret_cast<cx<float>*>(smem_raw);  // [nmax] source values
@@ -522,9 +523,9 @@ struct DenseArgs {
   int64_t ne;
 };
 
-// One CTA per (target leaf, listed frequency): lanes over 32 targets at a time, the four warps
-// over interleaved source elements of the leaf's dense blocks; the four partial sums of a target
-// are added in shared memory and then to the FP64 far-field sums.
+// One CTA per (group of a target leaf's dense source leaves, listed frequency): lanes over 32
+// targets at a time, the four warps over interleaved source elements of the group's blocks; the
+// four partial sums of a target are added in shared memory and then to the FP64 far-field sums.
 __global__ void __launch_bounds__(kDenseThreads) dense_apply_kernel(const DenseArgs a) {
   __shared__ cx<float> red[kDenseThreads / 32][32][3];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -632,10 +633,13 @@ static void ensure_structure(bem_ctx* ctx) {
     std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
     for (int64_t b = 0; b < H.n_lr; ++b) tblk[pos[LR[2 * b]]++] = (int32_t)b;
   }
+  // a CTA of the apply takes at most kGroupBlocks of a target's blocks: the groups of a large
+  // target would otherwise serialise many blocks in one CTA while few CTAs fill the GPU (one per
+  // target cluster: 490 CTAs on 5920 triangles, 26 % of the warps active)
   std::vector<int4> tgrp;
   for (int64_t c = 0; c < nc; ++c)
-    if (cnt[c + 1] > cnt[c])
-      tgrp.push_back(make_int4(t.begin[c], t.size[c], (int)cnt[c], (int)(cnt[c + 1] - cnt[c])));
+    for (int64_t q = cnt[c]; q < cnt[c + 1]; q += kGroupBlocks)
+      tgrp.push_back(make_int4(t.begin[c], t.size[c], (int)q, (int)std::min<int64_t>(kGroupBlocks, cnt[c + 1] - q)));
   H.n_tg = (int64_t)tgrp.size();
   // dense blocks grouped by target leaf
   std::vector<int64_t> dc(nc + 1, 0);
@@ -658,8 +662,8 @@ static void ensure_structure(bem_ctx* ctx) {
   }
   std::vector<int4> dgrp;
   for (int64_t c = 0; c < nc; ++c)
-    if (dc[c + 1] > dc[c])
-      dgrp.push_back(make_int4(t.begin[c], t.size[c], (int)dc[c], (int)(dc[c + 1] - dc[c])));
+    for (int64_t q = dc[c]; q < dc[c + 1]; q += kGroupBlocks)
+      dgrp.push_back(make_int4(t.begin[c], t.size[c], (int)q, (int)std::min<int64_t>(kGroupBlocks, dc[c + 1] - q)));
   H.n_dg = (int64_t)dgrp.size();
   upload(ctx, H.perm, t.perm);
   upload(ctx, H.lr, lr);
