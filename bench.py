@@ -890,6 +890,7 @@ def main():
         return
     if args.workload == "large":
         workload_large()
+        return
     if args.workload == "large-hmatrix":
         workload_large(hmatrix=dict(leaf=32, eta=2.0, max_block=512, max_rank=128, eps=args.hm_eps,
                                     max_freqs=args.hm_max_freqs))

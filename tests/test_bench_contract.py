@@ -44,3 +44,24 @@ def test_command_line_parses():
     assert p.returncode == 0, p.stderr
     for opt in ("--gpus", "--steps", "--warmup", "--impl", "--workload", "--afs-tol"):
         assert opt in p.stdout
+
+
+def test_every_side_workload_returns_without_running_the_benchmark(monkeypatch):
+    import sys
+    calls = []
+    for name in ("kernel_case", "kernel_case_single", "profile_step", "hm_kernel_case", "workload_uneven",
+                 "workload_porous_afs", "workload_example3", "workload_large", "run_gpu", "run_reference"):
+        monkeypatch.setattr(bench, name, lambda *a, _n=name, **k: calls.append(_n))
+    flags = [["--kernel-case"], ["--kernel-case-single"], ["--profile-step"], ["--hm-kernel-case"]]
+    flags += [["--workload", w] for w in ("uneven", "porous-afs", "porous-afs-full", "example3", "example3-mlp",
+                                          "large", "large-hmatrix", "porous-afs-lowband",
+                                          "porous-afs-full-lowband", "example3-lowband")]
+    for f in flags:
+        calls.clear()
+        monkeypatch.setattr(sys, "argv", ["bench.py", *f])
+        bench.main()
+        assert len(calls) == 1 and calls[0] not in ("run_gpu", "run_reference"), (f, calls)
+    calls.clear()
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    bench.main()
+    assert calls == ["run_gpu"]
