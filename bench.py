@@ -610,6 +610,9 @@ AFS_TOL = TOL    # residual tolerance of the AFS samples (--afs-tol; see afs_vs_
 AFS_WARM = None  # warm start of the AFS samples (--afs-warm; None: the workload's own choice)
 
 
+HMATRIX = None   # bem_hmatrix_params fields for the AFS-vs-FSM workloads (--hmatrix)
+
+
 def afs_vs_fsm(label, pb, dofs, n_orf, period, nc, J0, warm, restart=200, extra=None, max_samples=None):
     """AFS (Sec. 3) against the FSM (Sec. 2.2) on one problem through the library: the FSM solves
     the nc frequencies eta + i k 2 pi / period at once; AFS samples the same band [0, Omega],
@@ -631,6 +634,9 @@ def afs_vs_fsm(label, pb, dofs, n_orf, period, nc, J0, warm, restart=200, extra=
     c.set_bc(pb["bc_type"], pb["bc_value"], P.BEM_PROFILE_STEP)
     c.set_options(precision=P.BEM_PREC_MIXED, tol=TOL, restart=restart, max_iters=6000, max_refine=20,
                   warm_start=P.BEM_WARM_ZERO)
+    if HMATRIX is not None:
+        c.set_hmatrix(True, **HMATRIX)
+        label += "; H-matrix far field in the FP32 inner operator"
     eta = 3.0 * math.log(10.0) / period
     omega = (nc - 1) * 2.0 * math.pi / period
     t = np.linspace(0.0, 0.5 * period, 201)
@@ -672,6 +678,8 @@ def afs_vs_fsm(label, pb, dofs, n_orf, period, nc, J0, warm, restart=200, extra=
             "nc_ratio_fsm_over_afs": nc / max(int(info["n_samples"]), 1)}
     if extra:
         line.update(extra)
+    if HMATRIX is not None:
+        line["hmatrix"] = {"params": HMATRIX, "info": c.hmatrix_info()}
     print(json.dumps(line), flush=True)
     c.close()
 
@@ -835,7 +843,7 @@ def workload_large(n_freq=8, hmatrix=None):
 
 
 def main():
-    global AFS_TOL, AFS_WARM
+    global AFS_TOL, AFS_WARM, HMATRIX
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
@@ -852,6 +860,8 @@ def main():
                     help="cross-approximation tolerance of the H-matrix workloads")
     ap.add_argument("--hm-max-freqs", type=int, default=2,
                     help="frequencies whose H-matrix factors are held at once (H-matrix workloads)")
+    ap.add_argument("--hmatrix", action="store_true",
+                    help="AFS-vs-FSM workloads: the FP32 inner operator uses the H-matrix far field")
     ap.add_argument("--hm-kernel-case", action="store_true",
                     help="run only the H-matrix apply case used for ncu captures")
     ap.add_argument("--kernel-case-single", action="store_true",
@@ -864,6 +874,8 @@ def main():
                     help="run one of the other workloads instead of the benchmark (own JSON line)")
     args = ap.parse_args()
     AFS_TOL = args.afs_tol
+    if args.hmatrix:
+        HMATRIX = dict(leaf=32, eta=2.0, max_block=512, max_rank=128, eps=args.hm_eps, max_freqs=args.hm_max_freqs)
     if args.afs_warm:
         AFS_WARM = {"zero": 0, "nearest": 1, "mlp": 2, "vf": 3}[args.afs_warm]
     if args.kernel_case:
