@@ -528,7 +528,8 @@ typedef struct bem_hmatrix_params {
                          ~1e-5 reach their rounding floor and blocks run to max_rank (capped) */
   int32_t max_freqs;  /* frequencies whose factors are held at once: a bem_solve_frequencies
                          or bem_fsm list longer than this is solved in consecutive chunks of
-                         max_freqs frequencies (default 0: the whole list at once)           */
+                         max_freqs frequencies (default 0: the whole list at once; the two
+                         passes of BEM_WARM_SWEEP are not chunked)                          */
   int32_t reserved[5];
 } bem_hmatrix_params;
 

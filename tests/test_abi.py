@@ -107,3 +107,17 @@ def test_noalloc_binding_refuses_bad_tensors_before_calling_the_library():
         with pytest.raises(ValueError) as e:
             P.bem_fsm_eval_noalloc(hh, 250.0, 0.04, tt, oo)
         assert word in str(e.value), (word, str(e.value))
+
+
+def test_hmatrix_defaults_and_null_arguments_without_gpu():
+    import paper_1511_04355_gb300 as P
+    lib = _lib()
+    p = P.bem_hmatrix_params()
+    assert lib.bem_default_hmatrix_params(ctypes.byref(p)) == 0
+    assert (p.enable, p.leaf, p.max_block, p.max_rank, p.eta, p.eps, p.max_freqs) == (0, 32, 512, 96, 2.0, 1e-4, 0)
+    assert lib.bem_default_hmatrix_params(None) == P.BEM_ERR_INVALID_ARG
+    counts = (ctypes.c_int64 * 3)()
+    assert lib.bem_hmatrix_partition(None, 0, None, 0, ctypes.byref(p), None, None, 0, None, 0, None, 0,
+                                     counts) == P.BEM_ERR_INVALID_ARG
+    assert lib.bem_last_error(None)
+    assert lib.bem_set_hmatrix(None, ctypes.byref(p)) == P.BEM_ERR_INVALID_ARG
